@@ -1,0 +1,341 @@
+"""Benchmark: GPU Huffman encoding pipeline (histogram -> codebook -> encode
+with fused deflate) on the HPC quantisation-code field, 512^3 u16 symbols.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload hpc_field|small_field]
+
+One step = one pass of the whole path over one field already resident in
+HBM.  `value` is GB/s of input (all ranks' input bytes / max rank time).
+`e2e` measures the same pass through the public binding from pinned host
+memory, host->device input copy and device->host copy of the encoded stream
+included.  With --gpus N > 1 (under torchrun) every rank encodes its own
+replica field: the encoder has no cross-GPU exchange.
+`--impl reference` times the CPU oracle (test infrastructure, single thread)
+on a bounded prefix of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (n, nbins, generator description)
+    "hpc_field": (512 ** 3, 1024, "u16 Laplace(512, b=2) + 1% uniform outliers over 1024 bins, seed 1"),
+    "small_field": (1 << 20, 1024, "u16 Gaussian(512, sigma=8) over 1024 bins, seed 0"),
+}
+
+
+def make_input(name: str, n: int | None = None, rank: int = 0) -> np.ndarray:
+    from paper_2010_10039_gb300 import synth
+    if name == "hpc_field":
+        return synth.laplace_field(n or 512 ** 3, seed=1, stream=rank)
+    if name == "small_field":
+        return synth.gaussian_field(n or (1 << 20), seed=0)
+    raise ValueError(name)
+
+
+def load_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = max(smax, float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- CPU oracle leg
+
+def oracle_leg(name: str, n_full: int, nbins: int, max_seconds: float = 15.0):
+    """Times the oracle (single thread) on a prefix of the workload; returns
+    (GB/s of input, sample description, symbols, seconds)."""
+    import oracle
+    oracle.build()
+    n = min(n_full, 1 << 24)
+    sym = make_input(name, n)
+    t0 = time.perf_counter()
+    h = oracle.histogram(sym, nbins)
+    book = oracle.codebook(h)
+    oracle.encode(sym, book, chunk_log2=10)
+    dt = time.perf_counter() - t0
+    # grow the sample while the whole leg stays within the time bound
+    while n < n_full and dt * (min(n_full, 4 * n) / n) < max_seconds:
+        n = min(n_full, 4 * n)
+        sym = make_input(name, n)
+        t0 = time.perf_counter()
+        h = oracle.histogram(sym, nbins)
+        book = oracle.codebook(h)
+        oracle.encode(sym, book, chunk_log2=10)
+        dt = time.perf_counter() - t0
+    gbs = n * sym.itemsize / dt / 1e9
+    return gbs, f"first {n} symbols of the workload, histogram+codebook+encode, 1 thread", n, dt
+
+
+def run_reference(args, world, rank):
+    name = args.workload
+    n_full, nbins, desc = WORKLOADS[name]
+    if rank != 0:
+        return
+    vals = []
+    samp = None
+    for i in range(args.warmup + args.steps):
+        gbs, samp, n, dt = oracle_leg(name, n_full, nbins, max_seconds=max(2.0, 60.0 / max(1, args.steps + args.warmup)))
+        if i >= args.warmup:
+            vals.append((gbs, dt))
+    value = statistics.median(v[0] for v in vals)
+    ms = statistics.median(v[1] for v in vals) * 1e3
+    line = {
+        "impl": "reference", "metric": "huffman_encode_input_GBps", "value": round(value, 4), "unit": "GB/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16", "data": "synthetic",
+        "config": {"workload": name, "n": n_full, "nbins": nbins, "input": desc},
+        "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": samp, "value": round(value, 4), "unit": "GB/s"},
+        "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU leg
+
+def run_ours(args, world, rank, local):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2010_10039_gb300 as huff
+
+    torch.cuda.set_device(local)
+    name = args.workload
+    n, nbins, desc = WORKLOADS[name]
+    sym_np = make_input(name, n, rank)
+    sym = torch.from_numpy(sym_np.view(np.int16)).cuda()
+    params = {"chunk_log2": args.chunk_log2}
+    pipe = huff.Pipeline(n, nbins, params)
+    stream = torch.cuda.current_stream()
+
+    # warm-up
+    for _ in range(args.warmup):
+        pipe.run(sym)
+    st = pipe.status()
+    if st != 0:
+        raise RuntimeError(f"device status {huff.STATUS.get(st, st)}")
+    torch.cuda.synchronize()
+    total_bits = int(pipe.total_bits.item())
+
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    l0 = huff.huff_launch_count()
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for k in range(K):
+        ev[k][0].record(stream)
+        pipe.run(sym, stages=("hist",))
+        ev[k][1].record(stream)
+        pipe.run(sym, stages=("codebook",))
+        ev[k][2].record(stream)
+        pipe.run(sym, stages=("encode",))
+        ev[k][3].record(stream)
+    stop.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = huff.huff_launch_count() - l0
+    clk = clocks.stop()
+    total_ms = start.elapsed_time(stop)
+    ms_step = max_over_ranks(total_ms / K, world)
+    st = pipe.status()
+    if st != 0:
+        raise RuntimeError(f"device status {huff.STATUS.get(st, st)}")
+
+    hist_ms = statistics.mean(ev[k][0].elapsed_time(ev[k][1]) for k in range(K))
+    cb_ms = statistics.mean(ev[k][1].elapsed_time(ev[k][2]) for k in range(K))
+    enc_ms = statistics.mean(ev[k][2].elapsed_time(ev[k][3]) for k in range(K))
+    in_bytes = n * 2
+    out_bytes = (total_bits + 31) // 32 * 4
+    nch = (n + (1 << args.chunk_log2) - 1) >> args.chunk_log2
+    off_bytes = (nch + 1) * 8
+    enc_alg = in_bytes + out_bytes + off_bytes
+    hist_alg = in_bytes + nbins * 4
+    peak, peak_kind = load_peak()
+    value = world * in_bytes / (ms_step * 1e-3) / 1e9
+
+    # end to end through the binding from pinned host memory
+    host_in = torch.from_numpy(sym_np.view(np.int16)).pin_memory()
+    host_out = torch.empty(pipe.out.numel(), dtype=torch.int32).pin_memory()
+    host_offs = torch.empty(pipe.offsets.numel(), dtype=torch.int64).pin_memory()
+    dev_in = torch.empty_like(sym)
+    e2e_steps = max(1, min(K, 5))
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        dev_in.copy_(host_in, non_blocking=True)
+        pipe.run(dev_in)
+        tb = int(pipe.total_bits.item())
+        nw = (tb + 31) // 32
+        host_out[:nw].copy_(pipe.out[:nw], non_blocking=True)
+        host_offs.copy_(pipe.offsets, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world)
+    e2e_val = world * in_bytes / e2e_s / 1e9
+
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        gbs, samp, _, _ = oracle_leg(name, n, nbins)
+        cpu = {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": samp}
+    enc_s = enc_ms * 1e-3
+    line = {
+        "metric": "huffman_encode_input_GBps",
+        "value": round(value, 3),
+        "unit": "GB/s",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_step, 5),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u16",
+        "data": "synthetic",
+        "config": {"workload": name, "n": n, "nbins": nbins, "input": desc, "chunk_log2": args.chunk_log2,
+                   "l2": "inputs larger than L2 (268 MB per step)", "parallelism": f"replicas{world}",
+                   "avg_bits": round(total_bits / n, 4)},
+        "stages_ms": {"histogram": round(hist_ms, 5), "codebook": round(cb_ms, 5), "encode": round(enc_ms, 5)},
+        "encode_only_GBps": round(in_bytes / enc_s / 1e9, 3),
+        "roofline": {"bound": "hbm", "kernel": "encode (a4-a6)", "achieved": round(enc_alg / enc_s / 1e9, 2),
+                     "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": round(enc_alg / enc_s / 1e9 / peak, 4), "traffic": None,
+                     "algorithmic_bytes": enc_alg},
+        "roofline_histogram": {"bound": "hbm", "achieved": round(hist_alg / (hist_ms * 1e-3) / 1e9, 2),
+                               "peak": peak, "unit": "GB/s",
+                               "frac": round(hist_alg / (hist_ms * 1e-3) / 1e9 / peak, 4)},
+        "e2e": {"value": round(e2e_val, 3), "unit": "GB/s", "h2d_bytes_per_step": in_bytes,
+                "d2h_bytes_per_step": out_bytes + off_bytes + 8},
+        "gpu_launches": launches,
+        "cpu_baseline": cpu,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="hpc_field", choices=sorted(WORKLOADS))
+    ap.add_argument("--chunk-log2", dest="chunk_log2", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

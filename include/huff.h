@@ -1,0 +1,196 @@
+/*
+ * libhuff: GPU Huffman encoding for sm_103a (GB300).
+ *
+ * The operations follow the encoder of "Revisiting Huffman Coding: Toward
+ * Extreme Performance on Modern GPU Architectures" (Tian et al.), whose
+ * problem statement (Sec. IV, introduction) splits encoding into four stages:
+ * a histogram of the input symbols, construction of a Huffman codebook from
+ * it, canonisation with the reverse (decode) tables, and encoding into one
+ * bitstream.  Each stage is one call below; the batched and served forms run
+ * the same stages over many inputs.
+ *
+ * Conventions shared by every call:
+ *  - Buffers named d_* are DEVICE pointers owned by the caller.  The library
+ *    never frees or keeps them beyond the call (the batch plan and the server
+ *    keep the pointers the caller registers with them, see there).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Compute calls are asynchronous and stream ordered; they never
+ *    synchronise with the host unless stated.
+ *  - Host-checkable errors (NULL pointers, unsupported sizes, dtype/nbins
+ *    mismatch) return immediately with no work enqueued.
+ *  - Data-dependent errors found on the device (a symbol >= nbins, a symbol
+ *    without codeword, too small an output buffer, a histogram summing to
+ *    2^32 or more, a device wait that gave up) are recorded as the FIRST
+ *    error in a sticky status word at the start of the caller's workspace;
+ *    kernels skip the offending writes and finish.  huff_get_status() reads
+ *    the word (it synchronises the stream).
+ *  - Symbols are little-endian unsigned integers of 1, 2 or 4 bytes.
+ *  - The bitstream is an array of uint32 words: bit 31 of word 0 is the first
+ *    stream bit, codewords are written most significant bit first, one after
+ *    another in input order (the paper's Merge operator, Sec. IV-C, places
+ *    a_{2k+1} right after a_{2k}); bits after the last codeword are zero.
+ */
+#ifndef HUFF_H
+#define HUFF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { HUFF_U8 = 1, HUFF_U16 = 2, HUFF_U32 = 4 } huff_dtype;
+
+typedef enum {
+    HUFF_OK = 0,
+    HUFF_ERR_INVALID_ARG = 1,      /* bad pointer, size or parameter                      */
+    HUFF_ERR_SYMBOL_RANGE = 2,     /* an input symbol is >= nbins                         */
+    HUFF_ERR_NOT_IN_CODEBOOK = 3,  /* an input symbol has no codeword (zero count)        */
+    HUFF_ERR_CAPACITY = 4,         /* the output buffer is too small                      */
+    HUFF_ERR_OOM = 5,              /* a library-owned allocation failed                   */
+    HUFF_ERR_TIMEOUT = 6,          /* a bounded device wait gave up                       */
+    HUFF_ERR_BUSY = 7,             /* the server has no room for the request              */
+    HUFF_ERR_CUDA = 8,             /* a CUDA runtime call failed                          */
+    HUFF_ERR_HIST_OVERFLOW = 9,    /* histogram counts sum to 2^32 or more                */
+    HUFF_ERR_NOT_FOUND = 10,       /* unknown ticket                                      */
+    HUFF_ERR_CANCELLED = 11        /* request dropped because the server shut down       */
+} huff_status;
+
+#define HUFF_MAX_LEN 64            /* codeword lengths are 1..HUFF_MAX_LEN               */
+#define HUFF_MAX_BINS 65536        /* alphabet sizes are 1..HUFF_MAX_BINS                */
+#define HUFF_CW_LEN_SHIFT 58       /* cw = code | (len << 58)                             */
+
+/*
+ * Codebook: one caller-allocated device buffer of huff_codebook_bytes(nbins)
+ * bytes, 16-byte aligned, laid out as
+ *     huff_codebook_header
+ *     uint64_t cw[nbins]           cw[s] = code | (len << 58); 0 = no codeword
+ *     uint32_t sorted_syms[nbins]  used symbols by (length, id); nused valid
+ * first/entry/count are indexed by code length (slot 0 unused):
+ *     count[l]  number of codewords of length l
+ *     first[l]  the numerically first (smallest) codeword of length l; every
+ *               l-bit prefix of a longer codeword is below it (Sec. IV-B2)
+ *     entry[l]  number of codewords shorter than l (index into sorted_syms)
+ * Codewords of one length are consecutive integers in ascending symbol id.
+ */
+typedef struct {
+    uint32_t nbins;
+    uint32_t max_len;              /* 0 when no symbol is used                            */
+    uint64_t first[HUFF_MAX_LEN + 1];
+    uint32_t entry[HUFF_MAX_LEN + 1];
+    uint32_t count[HUFF_MAX_LEN + 1];
+    uint32_t nused;
+    uint32_t status;               /* huff_status of the build (HUFF_OK or an error)     */
+    uint64_t total_bits;           /* sum over symbols of count * length: encoded size   */
+    uint64_t nsymbols;             /* sum of the counts the codebook was built from      */
+} huff_codebook_header;
+
+/* Encoder tunables (Sec. IV-C "Interface": ReduceShuffleMerge<M, r>). */
+typedef struct {
+    int32_t chunk_log2;    /* M: one chunk offset per 2^M symbols; 4..30; paper default 10     */
+    int32_t reduce_log2;   /* r: 2^r consecutive symbols merged per thread in registers;
+                              -1 = pick r from the average codeword length (Sec. IV-C rule)   */
+    int32_t block_threads; /* threads per CTA: 128, 256 or 512; 0 = default                   */
+    int32_t merge;         /* HUFF_MERGE_*                                                    */
+} huff_params;
+
+enum {
+    HUFF_MERGE_AUTO = 0,
+    HUFF_MERGE_SCAN = 1,     /* block scan of merged lengths, one scatter into shared memory  */
+    HUFF_MERGE_SHUFFLE = 2   /* the paper's log-step shuffle-merge in shared memory           */
+};
+
+/* Fills *p with the defaults (M = 10, r = auto, block = 0, merge = auto). */
+void huff_default_params(huff_params *p);
+
+/*
+ * Reduction factor rule of Sec. IV-C: floor(log2 beta) + r + 1 = log2(word_bits),
+ * clamped to [1, 5]; beta = average codeword length in bits.
+ */
+int huff_reduce_factor(double avg_bits, int word_bits);
+
+/* Bytes of the codebook buffer for an alphabet of nbins symbols. */
+size_t huff_codebook_bytes(uint32_t nbins);
+
+/* Bytes of output (uint32 words) that always suffice: ceil(n * max_len / 32). */
+uint64_t huff_max_output_words(uint64_t n, uint32_t max_len);
+
+/*
+ * Bytes of device workspace one histogram/codebook/encode sequence needs for
+ * inputs of up to n symbols over nbins bins with parameters *p (NULL =
+ * defaults).  The first 256 bytes hold the sticky status word.
+ */
+size_t huff_workspace_bytes(uint64_t n, uint32_t nbins, const huff_params *p);
+
+/* Clears the status word of a workspace (stream ordered).  Call once after allocating it. */
+huff_status huff_workspace_init(void *d_ws, void *stream);
+
+/*
+ * Histogram (Sec. IV-A): d_hist[k] = number of i < n with d_sym[i] == k.
+ *   d_sym   n symbols of `dtype`, any alignment (16-byte aligned is fastest)
+ *   n       < 2^32; 0 gives an all-zero histogram
+ *   nbins   1..65536 (<= 256 for HUFF_U8)
+ *   d_hist  nbins uint32, overwritten
+ * A symbol >= nbins records HUFF_ERR_SYMBOL_RANGE and is not counted.
+ */
+huff_status huff_histogram(const void *d_sym, uint64_t n, huff_dtype dtype, uint32_t nbins,
+                           uint32_t *d_hist, void *d_ws, void *stream);
+
+/*
+ * Codebook (Sec. IV-B, Algorithm 1): optimal Huffman code lengths for every
+ * symbol with a nonzero count, then canonical codewords and the First/Entry
+ * decode metadata, written to d_codebook (layout above).
+ * Ties: leaves ordered by (count, id); when a leaf and a joined node weigh
+ * the same the leaf is joined first (the two-queue rule); the result equals
+ * the serial two-queue construction bit for bit.
+ *   d_hist      nbins uint32 counts whose sum must be < 2^32
+ *   d_codebook  huff_codebook_bytes(nbins) bytes, 16-byte aligned
+ * A sum >= 2^32 records HUFF_ERR_HIST_OVERFLOW and writes an empty codebook.
+ */
+huff_status huff_build_codebook(const uint32_t *d_hist, uint32_t nbins, void *d_codebook,
+                                void *d_ws, void *stream);
+
+/*
+ * Encode (Sec. IV-C, reduce-merge and shuffle-merge; gathering into one dense
+ * stream as in Table I's "get blockwise code len" and "coalescing copy"):
+ *   d_sym              n symbols (< 2^32) of `dtype`
+ *   d_codebook         a codebook built for the same alphabet
+ *   nbins              its alphabet size (checked against the codebook on the device)
+ *   p                  tunables (NULL = defaults); they never change the output
+ *   d_out              out_capacity_words uint32; receives ceil(total_bits/32) words
+ *   d_chunk_bit_offset ceil(n / 2^M) + 1 uint64: bit position of symbol c*2^M;
+ *                      the last entry is total_bits
+ *   d_total_bits       one uint64
+ * A symbol >= nbins or without codeword records an error; so does a stream
+ * longer than the capacity (nothing is written past it).
+ */
+huff_status huff_encode(const void *d_sym, uint64_t n, huff_dtype dtype, const void *d_codebook,
+                        uint32_t nbins, const huff_params *p, uint32_t *d_out, uint64_t out_capacity_words,
+                        uint64_t *d_chunk_bit_offset, uint64_t *d_total_bits,
+                        void *d_ws, void *stream);
+
+/*
+ * Decode (Sec. IV-B2, treeless canonical decoding with First and Entry): one
+ * thread per chunk walks the stream from d_chunk_bit_offset[c].
+ *   d_out  n symbols of `dtype`
+ * An invalid code records HUFF_ERR_INVALID_ARG.
+ */
+huff_status huff_decode(const uint32_t *d_in, uint64_t total_bits, const uint64_t *d_chunk_bit_offset,
+                        int chunk_log2, uint64_t n, huff_dtype dtype, const void *d_codebook,
+                        uint32_t nbins, void *d_out, void *d_ws, void *stream);
+
+/* Synchronises `stream` and returns the first device error recorded in d_ws. */
+huff_status huff_get_status(const void *d_ws, void *stream);
+
+/* Short text for a status code (static storage). */
+const char *huff_status_string(huff_status s);
+
+/* Number of kernel launches this library has issued in this process. */
+uint64_t huff_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HUFF_H */

@@ -1,0 +1,254 @@
+"""Python binding of libhuff (GPU Huffman encoding for sm_103a).
+
+The functions below carry the names of the C-ABI in ``include/huff.h`` and
+only marshal arguments: torch tensors become device pointers, the current
+torch stream becomes the cudaStream_t, and a non-OK status raises
+``HuffError``.  Every step of the pipeline runs in the library's CUDA kernels;
+there is no CPU fallback.  If ``libhuff.so`` is missing, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhuff.so")
+
+HUFF_U8, HUFF_U16, HUFF_U32 = 1, 2, 4
+HUFF_MERGE_AUTO, HUFF_MERGE_SCAN, HUFF_MERGE_SHUFFLE = 0, 1, 2
+HUFF_MAX_LEN = 64
+HUFF_CW_LEN_SHIFT = 58
+CODEBOOK_HEADER_BYTES = 1072
+
+STATUS = {
+    0: "HUFF_OK", 1: "HUFF_ERR_INVALID_ARG", 2: "HUFF_ERR_SYMBOL_RANGE", 3: "HUFF_ERR_NOT_IN_CODEBOOK",
+    4: "HUFF_ERR_CAPACITY", 5: "HUFF_ERR_OOM", 6: "HUFF_ERR_TIMEOUT", 7: "HUFF_ERR_BUSY", 8: "HUFF_ERR_CUDA",
+    9: "HUFF_ERR_HIST_OVERFLOW", 10: "HUFF_ERR_NOT_FOUND", 11: "HUFF_ERR_CANCELLED",
+}
+STATUS_CODE = {v: k for k, v in STATUS.items()}
+
+
+class HuffError(RuntimeError):
+    def __init__(self, code: int, where: str = ""):
+        self.code = code
+        self.name = STATUS.get(code, str(code))
+        super().__init__(f"{where}: {self.name}" if where else self.name)
+
+
+class huff_params(ctypes.Structure):
+    _fields_ = [("chunk_log2", ctypes.c_int32), ("reduce_log2", ctypes.c_int32),
+                ("block_threads", ctypes.c_int32), ("merge", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libhuff.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libhuff.so is not built ({LIB_PATH}); run paper_2010_10039_gb300/build.py "
+                               "or __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, u64, u32, i32, sz = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_size_t
+        P = ctypes.POINTER(huff_params)
+        sig = {
+            "huff_default_params": (None, [P]),
+            "huff_reduce_factor": (i32, [ctypes.c_double, i32]),
+            "huff_codebook_bytes": (sz, [u32]),
+            "huff_max_output_words": (u64, [u64, u32]),
+            "huff_workspace_bytes": (sz, [u64, u32, P]),
+            "huff_workspace_init": (i32, [vp, vp]),
+            "huff_histogram": (i32, [vp, u64, i32, u32, vp, vp, vp]),
+            "huff_build_codebook": (i32, [vp, u32, vp, vp, vp]),
+            "huff_encode": (i32, [vp, u64, i32, vp, u32, P, vp, u64, vp, vp, vp, vp]),
+            "huff_decode": (i32, [vp, u64, vp, i32, u64, i32, vp, u32, vp, vp, vp]),
+            "huff_get_status": (i32, [vp, vp]),
+            "huff_status_string": (ctypes.c_char_p, [i32]),
+            "huff_launch_count": (u64, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+# ------------------------------------------------------------------ helpers
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        torch = _torch()
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def dtype_code(t) -> int:
+    """HUFF_U8/U16/U32 for a tensor's element size."""
+    torch = _torch()
+    size = t.element_size()
+    if t.dtype.is_floating_point or t.dtype == torch.bool or size not in (1, 2, 4):
+        raise TypeError(f"symbols must be 1/2/4-byte integers, got {t.dtype}")
+    return size
+
+
+def _check(rc: int, where: str) -> None:
+    if rc != 0:
+        raise HuffError(rc, where)
+
+
+def _params(p) -> huff_params:
+    if isinstance(p, huff_params):
+        return p
+    q = huff_params()
+    lib().huff_default_params(ctypes.byref(q))
+    if p:
+        for k, v in dict(p).items():
+            setattr(q, k, int(v))
+    return q
+
+
+# ------------------------------------------------------------------ C-ABI mirrors
+
+def huff_default_params() -> huff_params:
+    return _params(None)
+
+
+def huff_reduce_factor(avg_bits: float, word_bits: int = 32) -> int:
+    return lib().huff_reduce_factor(float(avg_bits), int(word_bits))
+
+
+def huff_codebook_bytes(nbins: int) -> int:
+    return lib().huff_codebook_bytes(nbins)
+
+
+def huff_max_output_words(n: int, max_len: int) -> int:
+    return lib().huff_max_output_words(n, max_len)
+
+
+def huff_workspace_bytes(n: int, nbins: int, params=None) -> int:
+    return lib().huff_workspace_bytes(n, nbins, ctypes.byref(_params(params)))
+
+
+def huff_workspace_init(ws, stream=None) -> None:
+    _check(lib().huff_workspace_init(_ptr(ws), _stream(stream)), "huff_workspace_init")
+
+
+def huff_histogram(sym, nbins: int, hist, ws, stream=None, n: int | None = None, dtype: int | None = None) -> None:
+    n = sym.numel() if n is None else n
+    dt = dtype_code(sym) if dtype is None else dtype
+    _check(lib().huff_histogram(_ptr(sym), n, dt, nbins, _ptr(hist), _ptr(ws), _stream(stream)), "huff_histogram")
+
+
+def huff_build_codebook(hist, nbins: int, codebook, ws, stream=None) -> None:
+    _check(lib().huff_build_codebook(_ptr(hist), nbins, _ptr(codebook), _ptr(ws), _stream(stream)),
+           "huff_build_codebook")
+
+
+def huff_encode(sym, codebook, nbins: int, out, offsets, total_bits, ws, params=None, stream=None,
+                n: int | None = None, dtype: int | None = None, capacity_words: int | None = None) -> None:
+    n = sym.numel() if n is None else n
+    dt = dtype_code(sym) if dtype is None else dtype
+    cap = out.numel() if capacity_words is None else capacity_words
+    p = _params(params)
+    _check(lib().huff_encode(_ptr(sym), n, dt, _ptr(codebook), nbins, ctypes.byref(p), _ptr(out), cap,
+                             _ptr(offsets), _ptr(total_bits), _ptr(ws), _stream(stream)), "huff_encode")
+
+
+def huff_decode(stream_words, total_bits: int, offsets, chunk_log2: int, n: int, dtype: int, codebook, nbins: int,
+                out, ws, stream=None) -> None:
+    _check(lib().huff_decode(_ptr(stream_words), total_bits, _ptr(offsets), chunk_log2, n, dtype, _ptr(codebook),
+                             nbins, _ptr(out), _ptr(ws), _stream(stream)), "huff_decode")
+
+
+def huff_get_status(ws, stream=None) -> int:
+    return lib().huff_get_status(_ptr(ws), _stream(stream))
+
+
+def huff_status_string(code: int) -> str:
+    return lib().huff_status_string(code).decode()
+
+
+def huff_launch_count() -> int:
+    return lib().huff_launch_count()
+
+
+# ------------------------------------------------------------------ codebook view
+
+def parse_codebook(buf_cpu, nbins: int) -> dict:
+    """Splits a codebook buffer copied to the host (uint8 tensor or numpy array)
+    into its fields (layout of include/huff.h)."""
+    import numpy as np
+    b = np.asarray(buf_cpu.cpu().numpy() if hasattr(buf_cpu, "cpu") else buf_cpu, dtype=np.uint8)
+    hdr = b[:CODEBOOK_HEADER_BYTES]
+    u32 = hdr.view(np.uint32)
+    out = {"nbins": int(u32[0]), "max_len": int(u32[1])}
+    out["first"] = hdr[8:8 + 520].view(np.uint64).copy()
+    out["entry"] = hdr[528:528 + 260].view(np.uint32).copy()
+    out["count"] = hdr[788:788 + 260].view(np.uint32).copy()
+    out["nused"] = int(hdr[1048:1052].view(np.uint32)[0])
+    out["status"] = int(hdr[1052:1056].view(np.uint32)[0])
+    out["total_bits"] = int(hdr[1056:1064].view(np.uint64)[0])
+    out["nsymbols"] = int(hdr[1064:1072].view(np.uint64)[0])
+    cw = b[CODEBOOK_HEADER_BYTES:CODEBOOK_HEADER_BYTES + 8 * nbins].view(np.uint64).copy()
+    out["cw"] = cw
+    out["len"] = (cw >> np.uint64(HUFF_CW_LEN_SHIFT)).astype(np.uint8)
+    out["code"] = cw & np.uint64((1 << HUFF_CW_LEN_SHIFT) - 1)
+    ss = b[CODEBOOK_HEADER_BYTES + 8 * nbins:CODEBOOK_HEADER_BYTES + 12 * nbins].view(np.uint32)
+    out["sorted_syms"] = ss[:out["nused"]].copy()
+    return out
+
+
+# ------------------------------------------------------------------ whole pipeline
+
+class Pipeline:
+    """Device buffers (torch allocations) for histogram -> codebook -> encode of
+    inputs up to ``max_n`` symbols over ``nbins`` bins, reused across calls."""
+
+    def __init__(self, max_n: int, nbins: int, params=None, device="cuda", max_len_bound: int = 48):
+        torch = _torch()
+        self.nbins = nbins
+        self.params = _params(params)
+        self.max_n = max_n
+        self.device = torch.device(device)
+        self.hist = torch.empty(nbins, dtype=torch.int32, device=self.device)
+        self.codebook = torch.empty(huff_codebook_bytes(nbins), dtype=torch.uint8, device=self.device)
+        self.ws = torch.zeros(huff_workspace_bytes(max_n, nbins, self.params), dtype=torch.uint8, device=self.device)
+        cap = max(1, huff_max_output_words(max_n, max_len_bound))
+        self.out = torch.empty(cap, dtype=torch.int32, device=self.device)
+        nch = (max_n + (1 << self.params.chunk_log2) - 1) >> self.params.chunk_log2
+        self.offsets = torch.empty(nch + 1, dtype=torch.int64, device=self.device)
+        self.total_bits = torch.zeros(1, dtype=torch.int64, device=self.device)
+        huff_workspace_init(self.ws)
+
+    def run(self, sym, stream=None, stages=("hist", "codebook", "encode")) -> None:
+        n = sym.numel()
+        if n > self.max_n:
+            raise ValueError("input larger than the pipeline was sized for")
+        if "hist" in stages:
+            huff_histogram(sym, self.nbins, self.hist, self.ws, stream)
+        if "codebook" in stages:
+            huff_build_codebook(self.hist, self.nbins, self.codebook, self.ws, stream)
+        if "encode" in stages:
+            huff_encode(sym, self.codebook, self.nbins, self.out, self.offsets, self.total_bits, self.ws,
+                        self.params, stream)
+
+    def status(self, stream=None) -> int:
+        return huff_get_status(self.ws, stream)
