@@ -180,6 +180,33 @@ huff_status huff_decode(const uint32_t *d_in, uint64_t total_bits, const uint64_
                         int chunk_log2, uint64_t n, huff_dtype dtype, const void *d_codebook,
                         uint32_t nbins, void *d_out, void *d_ws, void *stream);
 
+/*
+ * Encode without any device allocation by the library or the caller's
+ * workspace.  The paper has no counterpart: this exists for callers that
+ * cannot allocate device memory -- e.g. code running inside another
+ * framework that owns every device allocation, or a loop that must not call
+ * cudaMalloc/cudaFree because they can synchronise the whole device.
+ * Same arguments and output as huff_encode, except:
+ *   - no d_ws: the encoder's scratch is a fixed device array inside the
+ *     library (2 MiB + 64 bytes, held on every GPU that loads the library
+ *     until the process exits);
+ *   - n may be at most 2^28 symbols (268,435,456); more returns
+ *     HUFF_ERR_INVALID_ARG with nothing enqueued;
+ *   - d_status: one caller-owned uint32 in device memory; the call sets it to
+ *     0 and the kernel records the first device error there (huff_status
+ *     codes), which the caller reads after synchronising.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Every call uses the same array and clears what it needs first, so
+ * calls that overlap on the GPU (other streams, other host threads) race and
+ * must be serialised by the caller.  No cudaMalloc, cudaFree or allocating
+ * library routine is called.
+ */
+huff_status huff_encode_noalloc(const void *d_sym, uint64_t n, huff_dtype dtype, const void *d_codebook,
+                                uint32_t nbins, const huff_params *p, uint32_t *d_out, uint64_t out_capacity_words,
+                                uint64_t *d_chunk_bit_offset, uint64_t *d_total_bits, uint32_t *d_status,
+                                void *stream);
+
 /* Synchronises `stream` and returns the first device error recorded in d_ws. */
 huff_status huff_get_status(const void *d_ws, void *stream);
 

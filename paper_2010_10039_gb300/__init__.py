@@ -64,6 +64,7 @@ def lib() -> ctypes.CDLL:
             "huff_build_codebook": (i32, [vp, u32, vp, vp, vp]),
             "huff_encode": (i32, [vp, u64, i32, vp, u32, P, vp, u64, vp, vp, vp, vp]),
             "huff_decode": (i32, [vp, u64, vp, i32, u64, i32, vp, u32, vp, vp, vp]),
+            "huff_encode_noalloc": (i32, [vp, u64, i32, vp, u32, P, vp, u64, vp, vp, vp, vp]),
             "huff_get_status": (i32, [vp, vp]),
             "huff_status_string": (ctypes.c_char_p, [i32]),
             "huff_launch_count": (u64, []),
@@ -170,6 +171,20 @@ def huff_encode(sym, codebook, nbins: int, out, offsets, total_bits, ws, params=
     p = _params(params)
     _check(lib().huff_encode(_ptr(sym), n, dt, _ptr(codebook), nbins, ctypes.byref(p), _ptr(out), cap,
                              _ptr(offsets), _ptr(total_bits), _ptr(ws), _stream(stream)), "huff_encode")
+
+
+def huff_encode_noalloc(sym, codebook, nbins: int, out, offsets, total_bits, status, params=None, stream=None,
+                        n: int | None = None, dtype: int | None = None, capacity_words: int | None = None) -> None:
+    """huff_encode with the library's fixed scratch instead of a workspace
+    (for callers that cannot allocate device memory); `status` is one device
+    uint32 that receives the first device error."""
+    n = sym.numel() if n is None else n
+    dt = dtype_code(sym) if dtype is None else dtype
+    cap = out.numel() if capacity_words is None else capacity_words
+    p = _params(params)
+    _check(lib().huff_encode_noalloc(_ptr(sym), n, dt, _ptr(codebook), nbins, ctypes.byref(p), _ptr(out), cap,
+                                     _ptr(offsets), _ptr(total_bits), _ptr(status), _stream(stream)),
+           "huff_encode_noalloc")
 
 
 def huff_decode(stream_words, total_bits: int, offsets, chunk_log2: int, n: int, dtype: int, codebook, nbins: int,

@@ -1,0 +1,83 @@
+// huff_encode_noalloc: the encode of huff_encode for callers that cannot
+// allocate device memory at all -- for example a plugin inside a host program
+// whose framework owns every device allocation, or a latency-critical loop
+// where cudaMalloc/cudaFree (which may synchronise the device) are not
+// allowed.  The encoder's scratch (a tile counter and one 16-byte look-back
+// descriptor per tile) lives in a fixed array in this file instead of a
+// caller workspace.
+#include <mutex>
+
+#include "common.cuh"
+
+namespace huff {
+
+huff_status encode_launch(const void *, uint64_t, huff_dtype, const void *, uint32_t, int, int, uint32_t *, uint64_t,
+                          uint64_t *, uint64_t *, uint8_t *, uint32_t *, cudaStream_t);
+size_t encode_scratch_bytes(uint64_t n);
+int encode_run_log2(huff_dtype dtype);
+
+// Largest input of one call, and the encoder scratch it needs (2 MiB + 64
+// bytes: a tile counter and a 16-byte descriptor per tile of >= 2048 symbols).
+constexpr uint64_t kNoAllocMaxSymbols = 1ull << 28;
+constexpr size_t kNoAllocScratchBytes = 64 + 16 * (kNoAllocMaxSymbols / 2048);
+
+// One copy per device that loads the library; it stays until the process exits.
+static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+static uint8_t *g_scratch_addr[kMaxDevices];
+static std::mutex g_scratch_mu;
+
+// Device address of the array on the current device (looked up once per device).
+static uint8_t *noalloc_scratch(huff_status *err) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        *err = HUFF_ERR_CUDA;
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
+            *err = HUFF_ERR_CUDA;
+            return nullptr;
+        }
+        g_scratch_addr[dev] = static_cast<uint8_t *>(ptr);
+    }
+    return g_scratch_addr[dev];
+}
+
+}  // namespace huff
+
+using namespace huff;
+
+extern "C" huff_status huff_encode_noalloc(const void *d_sym, uint64_t n, huff_dtype dtype, const void *d_codebook,
+                                           uint32_t nbins, const huff_params *p, uint32_t *d_out,
+                                           uint64_t out_capacity_words, uint64_t *d_chunk_bit_offset,
+                                           uint64_t *d_total_bits, uint32_t *d_status, void *stream) {
+    huff_params prm;
+    huff_default_params(&prm);
+    if (p) prm = *p;
+    if (n > kNoAllocMaxSymbols) return HUFF_ERR_INVALID_ARG;          // beyond the fixed scratch
+    if (!d_status || !d_codebook || !d_chunk_bit_offset || !d_total_bits || (n && (!d_sym || !d_out)))
+        return HUFF_ERR_INVALID_ARG;
+    if (dtype != HUFF_U8 && dtype != HUFF_U16 && dtype != HUFF_U32) return HUFF_ERR_INVALID_ARG;
+    if (nbins < 1 || nbins > HUFF_MAX_BINS || (dtype == HUFF_U8 && nbins > 256)) return HUFF_ERR_INVALID_ARG;
+    if (((uintptr_t)d_codebook & 15) != 0) return HUFF_ERR_INVALID_ARG;
+    if (prm.chunk_log2 < 4 || prm.chunk_log2 > 30 || prm.chunk_log2 < encode_run_log2(dtype)) return HUFF_ERR_INVALID_ARG;
+    if (prm.reduce_log2 != -1 && (prm.reduce_log2 < 0 || prm.reduce_log2 > prm.chunk_log2)) return HUFF_ERR_INVALID_ARG;
+    huff_status err = HUFF_OK;
+    uint8_t *scratch = noalloc_scratch(&err);
+    if (!scratch) return err;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(d_status, 0, sizeof(uint32_t), st) != cudaSuccess) return HUFF_ERR_CUDA;
+    if (n == 0) {
+        if (cudaMemsetAsync(d_chunk_bit_offset, 0, 8, st) != cudaSuccess) return HUFF_ERR_CUDA;
+        if (cudaMemsetAsync(d_total_bits, 0, 8, st) != cudaSuccess) return HUFF_ERR_CUDA;
+        return HUFF_OK;
+    }
+    // the encoder clears the part of the scratch it uses before its launch
+    if (encode_scratch_bytes(n) > kNoAllocScratchBytes) return HUFF_ERR_INVALID_ARG;
+    return encode_launch(d_sym, n, dtype, d_codebook, nbins, prm.chunk_log2, prm.reduce_log2, d_out,
+                         out_capacity_words, d_chunk_bit_offset, d_total_bits, scratch, d_status, st);
+}
