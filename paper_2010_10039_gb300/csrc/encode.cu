@@ -31,7 +31,7 @@ namespace huff {
 
 constexpr int kEncThreads = 256;           // merge threads (8 warps)
 constexpr int kEncRPT = 2;                 // consecutive 16-byte vectors per merge thread per sub-tile
-constexpr int kEncStages = 3;              // sub-tile stages in flight
+constexpr int kEncStages = 4;              // sub-tile stages in flight
 constexpr int kEncVecBytes = 16;
 constexpr int kEncSubBytes = kEncThreads * kEncRPT * kEncVecBytes;   // 8 KB per sub-tile
 constexpr int kEncMaxSubs = 8;             // sub-tiles per tile (fewer when codewords are long)
@@ -100,20 +100,6 @@ __device__ __forceinline__ void sym_from_vec(const uint4 &v, uint32_t *s, uint32
     s[0] = v.x; s[1] = v.y; s[2] = v.z; s[3] = v.w;
 }
 
-// Largest symbol of a 16-byte vector.
-__device__ __forceinline__ uint32_t vec_max(const uint4 &v, uint8_t) {
-    uint32_t m = __vmaxu4(__vmaxu4(v.x, v.y), __vmaxu4(v.z, v.w));
-    m = __vmaxu4(m, m >> 16);
-    return max(m & 0xFFu, (m >> 8) & 0xFFu);
-}
-__device__ __forceinline__ uint32_t vec_max(const uint4 &v, uint16_t) {
-    uint32_t m = __vmaxu2(__vmaxu2(v.x, v.y), __vmaxu2(v.z, v.w));
-    return max(m & 0xFFFFu, m >> 16);
-}
-__device__ __forceinline__ uint32_t vec_max(const uint4 &v, uint32_t) {
-    return max(max(v.x, v.y), max(v.z, v.w));
-}
-
 // ---------------------------------------------------------------- codebook entries
 // u32 form (codewords up to 23 bits): len << 24 | code, kBad32 for no codeword.
 // u64 form: the codebook's cw (len << 58 | code), 0 for no codeword.
@@ -142,15 +128,32 @@ __device__ __forceinline__ uint64_t ent_code<uint32_t>(uint32_t e) { return e & 
 template <>
 __device__ __forceinline__ uint64_t ent_code<uint64_t>(uint64_t e) { return e & ((1ull << HUFF_CW_LEN_SHIFT) - 1); }
 
-// Entry of symbol s; CHECKED tolerates s >= nbins (the slot at nbins has no codeword).
-template <typename Entry, bool GTAB, bool CHECKED>
-__device__ __forceinline__ Entry table_get(const Entry *tab, const uint64_t *gcw, uint32_t s, uint32_t nbins) {
+// Entry of symbol s.  The shared-memory table has a power-of-two number of
+// slots (tmask + 1 >= nbins, slots past nbins have no codeword) and is indexed
+// with s & tmask; a symbol beyond the table is caught by the vector range test.
+// The global table (large alphabets) is read only for s < nbins.
+template <typename Entry, bool GTAB>
+__device__ __forceinline__ Entry table_get(const Entry *tab, const uint64_t *gcw, uint32_t s, uint32_t nbins,
+                                           uint32_t tmask) {
     if (GTAB) {
-        uint64_t c = (!CHECKED || s < nbins) ? __ldg(gcw + s) : 0ull;
+        uint64_t c = s < nbins ? __ldg(gcw + s) : 0ull;
         return entry_from_cw<Entry>(c);
     } else {
-        return tab[CHECKED ? (s < nbins ? s : nbins) : s];
+        return tab[s & tmask];
     }
+}
+
+// True when some symbol of the vector is beyond a table of tmask + 1 slots.
+__device__ __forceinline__ bool vec_out_of_table(const uint4 &v, uint32_t tmask, uint8_t) {
+    const uint32_t m = tmask * 0x01010101u;
+    return ((v.x | v.y | v.z | v.w) & ~m) != 0;
+}
+__device__ __forceinline__ bool vec_out_of_table(const uint4 &v, uint32_t tmask, uint16_t) {
+    const uint32_t m = tmask | (tmask << 16);
+    return ((v.x | v.y | v.z | v.w) & ~m) != 0;
+}
+__device__ __forceinline__ bool vec_out_of_table(const uint4 &v, uint32_t tmask, uint32_t) {
+    return ((v.x | v.y | v.z | v.w) & ~tmask) != 0;
 }
 
 // acc = acc (+) codeword: append l bits (one step of reduce-merge).
@@ -306,6 +309,7 @@ __device__ uint64_t lookback_warp(const EncArgs &a, uint64_t j, uint64_t L, uint
 // tile is under way.
 struct Producer {
     uint64_t tile;      // tile being fetched
+    uint64_t next;      // id of the tile after it (taken one tile ahead, so its latency is hidden)
     uint32_t sub;       // next sub-tile of it to fetch
     uint32_t slot;      // next ring slot
 };
@@ -315,7 +319,8 @@ __device__ __forceinline__ void produce_next(const EncArgs &a, Producer &p, uint
                                              uint8_t *stage, uint64_t *bars, volatile uint64_t *s_stage_tile) {
     constexpr uint32_t SUB = enc_sub_syms<Sym>();
     if (p.sub >= nsub && p.tile < ntiles) {
-        p.tile = atomicAdd(a.tile_counter, 1u);
+        p.tile = p.next;
+        p.next = p.tile < ntiles ? atomicAdd(a.tile_counter, 1u) : p.tile;
         p.sub = 0;
     }
     const int s = (int)(p.slot % kEncStages);
@@ -369,8 +374,8 @@ struct EncShared {
 // collects kBad32 when a valid position has no codeword.
 template <typename Sym, typename Entry, bool GTAB, int R2, bool FULL>
 __device__ __forceinline__ uint32_t merge_vec(const uint32_t *sv, uint32_t valid, const Entry *tab,
-                                              const uint64_t *gcw, uint32_t nbins, uint64_t *acc, uint32_t *rb,
-                                              uint32_t &bad) {
+                                              const uint64_t *gcw, uint32_t nbins, uint32_t tmask, uint64_t *acc,
+                                              uint32_t *rb, uint32_t &bad) {
     constexpr int V = VecOf<Sym>::N;
     constexpr int RL = 1 << R2;
     constexpr int NR = V / RL;
@@ -382,7 +387,7 @@ __device__ __forceinline__ uint32_t merge_vec(const uint32_t *sv, uint32_t valid
 #pragma unroll
         for (int x = 0; x < RL; x++) {
             const int xi = r * RL + x;
-            Entry en = table_get<Entry, GTAB, !FULL>(tab, gcw, sv[xi], nbins);
+            Entry en = table_get<Entry, GTAB>(tab, gcw, sv[xi], nbins, tmask);
             if (!FULL && xi >= (int)valid) en = (Entry)0;            // padding past n: length 0
             else if (sizeof(Entry) == 4) bad |= (uint32_t)en;
             else bad |= en == 0 ? kBad32 : 0u;
@@ -402,7 +407,7 @@ __device__ __forceinline__ uint32_t merge_vec(const uint32_t *sv, uint32_t valid
 // 2^r codewords per register.
 template <typename Sym, typename Entry, bool GTAB, int R2>
 __device__ void merge_warps(const EncArgs &a, uint8_t *stage, uint32_t *ring, const Entry *tab, uint32_t nbins,
-                            uint32_t nsub, uint32_t max_len, EncShared &S) {
+                            uint32_t tmask, uint32_t nsub, uint32_t max_len, EncShared &S) {
     constexpr int V = VecOf<Sym>::N;              // symbols per 16-byte vector
     constexpr int RL = 1 << R2;                   // symbols per merged run
     constexpr int NR = V / RL;                    // runs per vector
@@ -428,8 +433,11 @@ __device__ void merge_warps(const EncArgs &a, uint8_t *stage, uint32_t *ring, co
     prod.slot = 0;
     prod.sub = nsub;
     prod.tile = 0;
-    if (tid == 0)
+    prod.next = 0;
+    if (tid == 0) {
+        prod.next = atomicAdd(a.tile_counter, 1u);
         for (int i = 0; i < kEncStages; i++) produce_next<Sym>(a, prod, nsub, ntiles, stage, S.bars, stage_tile);
+    }
     merge_sync();
 
     uint32_t it = 0, t = 0, base = 0;
@@ -478,17 +486,18 @@ __device__ void merge_warps(const EncArgs &a, uint8_t *stage, uint32_t *ring, co
                 if (full) {
                     const uint4 v = *reinterpret_cast<const uint4 *>(st + q * kEncVecBytes);
                     sym_from_vec(v, sv, Sym());
-                    if (vec_max(v, Sym()) < nbins)
-                        bits[k] = merge_vec<Sym, Entry, GTAB, R2, true>(sv, V, tab, gcw, nbins, acc[k], rb[k], bad);
-                    else
-                        bits[k] = merge_vec<Sym, Entry, GTAB, R2, false>(sv, V, tab, gcw, nbins, acc[k], rb[k], bad);
+                    if (!GTAB && vec_out_of_table(v, tmask, Sym())) bad |= kBad32;
+                    bits[k] = merge_vec<Sym, Entry, GTAB, R2, true>(sv, V, tab, gcw, nbins, tmask, acc[k], rb[k], bad);
                 } else {
                     const Sym *sp = reinterpret_cast<const Sym *>(a.sym);
                     const uint64_t i0 = s0 + (uint64_t)q * V;
                     const uint32_t vl = i0 >= a.n ? 0 : (a.n - i0 < V ? (uint32_t)(a.n - i0) : V);
 #pragma unroll
                     for (int x = 0; x < V; x++) sv[x] = x < (int)vl ? (uint32_t)sp[i0 + x] : 0u;
-                    bits[k] = merge_vec<Sym, Entry, GTAB, R2, false>(sv, vl, tab, gcw, nbins, acc[k], rb[k], bad);
+#pragma unroll
+                    for (int x = 0; x < V; x++)
+                        if (x < (int)vl && sv[x] > tmask) bad |= kBad32;
+                    bits[k] = merge_vec<Sym, Entry, GTAB, R2, false>(sv, vl, tab, gcw, nbins, tmask, acc[k], rb[k], bad);
                 }
             }
             if (bad & kBad32) {
@@ -558,7 +567,7 @@ __device__ void merge_warps(const EncArgs &a, uint8_t *stage, uint32_t *ring, co
                             if (i >= a.n) break;
                             // the stage may be refilled already: read the symbol from global memory
                             const uint32_t sx = (uint32_t)reinterpret_cast<const Sym *>(a.sym)[i];
-                            Entry en = table_get<Entry, GTAB, true>(tab, gcw, sx, nbins);
+                            Entry en = table_get<Entry, GTAB>(tab, gcw, sx, nbins, tmask);
                             const uint32_t l = ent_len<Entry>(en);
                             if (l) sink.put64(ent_code<Entry>(en), l);
                         }
@@ -720,13 +729,13 @@ __device__ __forceinline__ int pick_r(const EncArgs &a, const huff_codebook_head
 
 template <typename Sym, typename Entry, bool GTAB>
 __device__ void merge_dispatch(int r, const EncArgs &a, uint8_t *stage, uint32_t *ring, const Entry *tab,
-                               uint32_t nbins, uint32_t nsub, uint32_t max_len, EncShared &S) {
+                               uint32_t nbins, uint32_t tmask, uint32_t nsub, uint32_t max_len, EncShared &S) {
     switch (r) {
-        case 0: if constexpr (VecOf<Sym>::N <= 4) merge_warps<Sym, Entry, GTAB, 0>(a, stage, ring, tab, nbins, nsub, max_len, S); break;
-        case 1: if constexpr (VecOf<Sym>::N <= 4) merge_warps<Sym, Entry, GTAB, 1>(a, stage, ring, tab, nbins, nsub, max_len, S); break;
-        case 2: merge_warps<Sym, Entry, GTAB, 2>(a, stage, ring, tab, nbins, nsub, max_len, S); break;
-        case 3: if constexpr (VecOf<Sym>::N >= 8) merge_warps<Sym, Entry, GTAB, 3>(a, stage, ring, tab, nbins, nsub, max_len, S); break;
-        default: if constexpr (VecOf<Sym>::N >= 16) merge_warps<Sym, Entry, GTAB, 4>(a, stage, ring, tab, nbins, nsub, max_len, S); break;
+        case 0: if constexpr (VecOf<Sym>::N <= 4) merge_warps<Sym, Entry, GTAB, 0>(a, stage, ring, tab, nbins, tmask, nsub, max_len, S); break;
+        case 1: if constexpr (VecOf<Sym>::N <= 4) merge_warps<Sym, Entry, GTAB, 1>(a, stage, ring, tab, nbins, tmask, nsub, max_len, S); break;
+        case 2: merge_warps<Sym, Entry, GTAB, 2>(a, stage, ring, tab, nbins, tmask, nsub, max_len, S); break;
+        case 3: if constexpr (VecOf<Sym>::N >= 8) merge_warps<Sym, Entry, GTAB, 3>(a, stage, ring, tab, nbins, tmask, nsub, max_len, S); break;
+        default: if constexpr (VecOf<Sym>::N >= 16) merge_warps<Sym, Entry, GTAB, 4>(a, stage, ring, tab, nbins, tmask, nsub, max_len, S); break;
     }
 }
 
@@ -750,13 +759,16 @@ __global__ void __launch_bounds__(kEncCtaThreads, sizeof(Sym) == 1 ? 2 : 3) enco
         return;
     }
     for (uint32_t i = threadIdx.x; i < RW; i += blockDim.x) ring[i] = 0;
+    uint32_t tslots = 1;
+    while (tslots < nbins) tslots <<= 1;
+    const uint32_t tmask = tslots - 1;
     if (!GTAB) {
         if (small) {
             uint32_t *t32 = reinterpret_cast<uint32_t *>(tab);
-            for (uint32_t i = threadIdx.x; i <= nbins; i += blockDim.x)
+            for (uint32_t i = threadIdx.x; i < tslots; i += blockDim.x)
                 t32[i] = entry_from_cw<uint32_t>(i < nbins ? gcw[i] : 0ull);
         } else {
-            for (uint32_t i = threadIdx.x; i <= nbins; i += blockDim.x) tab[i] = i < nbins ? gcw[i] : 0ull;
+            for (uint32_t i = threadIdx.x; i < tslots; i += blockDim.x) tab[i] = i < nbins ? gcw[i] : 0ull;
         }
     }
     if (threadIdx.x == 0) {
@@ -782,10 +794,10 @@ __global__ void __launch_bounds__(kEncCtaThreads, sizeof(Sym) == 1 ? 2 : 3) enco
     }
     const int r = pick_r<Sym>(a, hdr);
     if (small)
-        merge_dispatch<Sym, uint32_t, GTAB>(r, a, stage, ring, reinterpret_cast<const uint32_t *>(tab), nbins, nsub,
-                                            max_len, S);
+        merge_dispatch<Sym, uint32_t, GTAB>(r, a, stage, ring, reinterpret_cast<const uint32_t *>(tab), nbins, tmask,
+                                            nsub, max_len, S);
     else
-        merge_dispatch<Sym, uint64_t, GTAB>(r, a, stage, ring, tab, nbins, nsub, max_len, S);
+        merge_dispatch<Sym, uint64_t, GTAB>(r, a, stage, ring, tab, nbins, tmask, nsub, max_len, S);
 }
 
 // ---------------------------------------------------------------- host side
@@ -798,7 +810,9 @@ size_t encode_scratch_bytes(uint64_t n) {
 
 template <typename Sym>
 static size_t enc_smem_bytes(bool gtab, uint32_t nbins) {
-    return kEncStages * kEncSubBytes + ring_words<Sym>() * 4 + (gtab ? 0 : (nbins + 1) * 8ull);
+    uint32_t tslots = 1;
+    while (tslots < nbins) tslots <<= 1;
+    return kEncStages * kEncSubBytes + ring_words<Sym>() * 4 + (gtab ? 0 : tslots * 8ull);
 }
 
 template <typename Sym>

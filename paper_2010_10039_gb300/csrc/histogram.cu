@@ -50,44 +50,54 @@ struct HistArgs {
     uint64_t head;            // symbols before the first 16-byte aligned address
     uint64_t nvec;            // whole 16-byte vectors after the head
     uint32_t nbins;
+    uint32_t mask;            // slots per replica - 1 (a power of two minus one, >= nbins - 1)
     uint32_t nrep;            // replicas (32-bit layout)
     uint32_t stride;          // words per replica
     uint32_t *hist;
     uint32_t *status;
 };
 
+// Counts one symbol without a branch: replicas have a power-of-two number of
+// slots (mask + 1 >= nbins) and symbols are masked into them; `seen` ORs the
+// symbols, so a symbol beyond the slots is caught after the loop, and one in
+// [nbins, mask] leaves a count in a slot past nbins (both are range errors).
 template <bool PACKED>
-__device__ __forceinline__ void count_one(uint32_t *h, uint32_t s, uint32_t nbins, uint32_t &bad) {
-    if (s < nbins) {
-        if (PACKED) atomicAdd(h + (s & (kPackedWords - 1)), 1u << ((s >> 15) << 4));
-        else atomicAdd(h + s, 1u);
-    } else {
-        bad = 1;
-    }
+__device__ __forceinline__ void count_one(uint32_t *h, uint32_t s, uint32_t mask, uint32_t &seen) {
+    seen |= s;
+    if (PACKED) atomicAdd(h + (s & (kPackedWords - 1)), 1u << (((s & mask) >> 15) << 4));
+    else atomicAdd(h + (s & mask), 1u);
 }
 
 template <typename Sym, bool PACKED>
-__device__ __forceinline__ void count_vec(uint32_t *h, const uint4 &v, uint32_t nbins, uint32_t &bad) {
+__device__ __forceinline__ void count_vec(uint32_t *h, const uint4 &v, uint32_t mask, uint32_t &seen) {
 #pragma unroll
-    for (int j = 0; j < SymVec<Sym>::N; j++) count_one<PACKED>(h, SymVec<Sym>::get(v, j), nbins, bad);
+    for (int j = 0; j < SymVec<Sym>::N; j++) count_one<PACKED>(h, SymVec<Sym>::get(v, j), mask, seen);
 }
 
+// Folds the shared-memory counts into the global histogram; counts in slots
+// at or past nbins are symbols out of range: they set *bad and are dropped.
 template <bool PACKED>
-__device__ void hist_flush(uint32_t *hsm, const HistArgs &a) {
+__device__ void hist_flush(uint32_t *hsm, const HistArgs &a, uint32_t &bad) {
     if (PACKED) {
         for (uint32_t w = threadIdx.x; w < kPackedWords; w += blockDim.x) {
             uint32_t v = hsm[w];
             if (v) {
-                if (v & 0xFFFFu) atomicAdd(a.hist + w, v & 0xFFFFu);
-                if (v >> 16) atomicAdd(a.hist + w + kPackedWords, v >> 16);
+                if (v & 0xFFFFu) {
+                    if (w < a.nbins) atomicAdd(a.hist + w, v & 0xFFFFu); else bad = 1;
+                }
+                if (v >> 16) {
+                    if (w + kPackedWords < a.nbins) atomicAdd(a.hist + w + kPackedWords, v >> 16); else bad = 1;
+                }
                 hsm[w] = 0;
             }
         }
     } else {
-        for (uint32_t k = threadIdx.x; k < a.nbins; k += blockDim.x) {
+        for (uint32_t k = threadIdx.x; k <= a.mask; k += blockDim.x) {
             uint32_t sum = 0;
             for (uint32_t r = 0; r < a.nrep; r++) sum += hsm[r * a.stride + k];
-            if (sum) atomicAdd(a.hist + k, sum);
+            if (sum) {
+                if (k < a.nbins) atomicAdd(a.hist + k, sum); else bad = 1;
+            }
         }
     }
 }
@@ -96,10 +106,11 @@ template <typename Sym, bool PACKED>
 __global__ void __launch_bounds__(kHistThreads, 2) hist_kernel(HistArgs a) {
     extern __shared__ __align__(16) uint32_t hsm[];
     const uint32_t words = PACKED ? kPackedWords : a.nrep * a.stride;
+    const uint32_t mask = a.mask;
     for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) hsm[i] = 0;
     __syncthreads();
     uint32_t *my = PACKED ? hsm : hsm + ((threadIdx.x >> 5) % a.nrep) * a.stride;
-    uint32_t bad = 0;
+    uint32_t seen = 0, bad = 0;
 
     const uint4 *vec = reinterpret_cast<const uint4 *>(a.base + a.head * sizeof(Sym));
     constexpr uint64_t kRound = 2ull * kHistThreads;              // vectors per CTA round
@@ -112,21 +123,21 @@ __global__ void __launch_bounds__(kHistThreads, 2) hist_kernel(HistArgs a) {
         const uint64_t i0 = r * kRound + threadIdx.x, i1 = i0 + kHistThreads;
         if (i1 < a.nvec) {
             uint4 v0 = vec[i0], v1 = vec[i1];
-            count_vec<Sym, PACKED>(my, v0, a.nbins, bad);
-            count_vec<Sym, PACKED>(my, v1, a.nbins, bad);
+            count_vec<Sym, PACKED>(my, v0, mask, seen);
+            count_vec<Sym, PACKED>(my, v1, mask, seen);
         } else if (i0 < a.nvec) {
-            count_vec<Sym, PACKED>(my, vec[i0], a.nbins, bad);
+            count_vec<Sym, PACKED>(my, vec[i0], mask, seen);
         }
         if (PACKED && ++since == kRoundsPerEpoch) {
             __syncthreads();
-            hist_flush<true>(hsm, a);
+            hist_flush<true>(hsm, a, bad);
             __syncthreads();
             since = 0;
         }
     }
     if (PACKED) {
         __syncthreads();
-        hist_flush<true>(hsm, a);
+        hist_flush<true>(hsm, a, bad);
         __syncthreads();
     }
     // head (before the first aligned address) and tail (after the last whole vector)
@@ -135,11 +146,11 @@ __global__ void __launch_bounds__(kHistThreads, 2) hist_kernel(HistArgs a) {
     const uint64_t nrest = a.head + (a.n - tail0);
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nrest; i += (uint64_t)gridDim.x * blockDim.x) {
         uint64_t idx = i < a.head ? i : tail0 + (i - a.head);
-        count_one<PACKED>(my, sp[idx], a.nbins, bad);
+        count_one<PACKED>(my, sp[idx], mask, seen);
     }
-    if (bad) set_error(a.status, HUFF_ERR_SYMBOL_RANGE);
     __syncthreads();
-    hist_flush<PACKED>(hsm, a);
+    hist_flush<PACKED>(hsm, a, bad);
+    if (bad || seen > mask) set_error(a.status, HUFF_ERR_SYMBOL_RANGE);
 }
 
 template <typename Sym>
@@ -156,6 +167,9 @@ static huff_status launch_hist(const void *d_sym, uint64_t n, uint32_t nbins, ui
     a.hist = d_hist;
     a.status = status;
     const bool packed = nbins > 16384;
+    uint32_t slots = 1;
+    while (slots < nbins) slots <<= 1;
+    a.mask = slots - 1;
     size_t smem;
     if (packed) {
         a.nrep = 1;
@@ -163,7 +177,7 @@ static huff_status launch_hist(const void *d_sym, uint64_t n, uint32_t nbins, ui
         smem = kPackedWords * 4;
     } else {
         // one replica per warp, padded so one bin of different replicas hits different banks
-        a.stride = ((nbins + 31) / 32) * 32 + 1;
+        a.stride = slots + 1;
         const uint32_t warps = kHistThreads / 32;
         uint32_t r = (uint32_t)((100 * 1024) / (a.stride * 4ull));
         a.nrep = r > warps ? warps : (r < 1 ? 1 : r);
