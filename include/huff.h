@@ -24,7 +24,9 @@
  *    error in a sticky status word at the start of the caller's workspace;
  *    kernels skip the offending writes and finish.  huff_get_status() reads
  *    the word (it synchronises the stream).
- *  - Symbols are little-endian unsigned integers of 1, 2 or 4 bytes.
+ *  - Symbols are little-endian unsigned integers of 1, 2 or 4 bytes; every
+ *    typed device array must be aligned to its element size (a misaligned
+ *    pointer returns HUFF_ERR_INVALID_ARG).
  *  - The bitstream is an array of uint32 words: bit 31 of word 0 is the first
  *    stream bit, codewords are written most significant bit first, one after
  *    another in input order (the paper's Merge operator, Sec. IV-C, places
@@ -128,7 +130,7 @@ huff_status huff_workspace_init(void *d_ws, void *stream);
 
 /*
  * Histogram (Sec. IV-A): d_hist[k] = number of i < n with d_sym[i] == k.
- *   d_sym   n symbols of `dtype`, any alignment (16-byte aligned is fastest)
+ *   d_sym   n symbols of `dtype`, aligned to the element size (16-byte aligned is fastest)
  *   n       < 2^32; 0 gives an all-zero histogram
  *   nbins   1..65536 (<= 256 for HUFF_U8)
  *   d_hist  nbins uint32, overwritten
@@ -206,6 +208,86 @@ huff_status huff_encode_noalloc(const void *d_sym, uint64_t n, huff_dtype dtype,
                                 uint32_t nbins, const huff_params *p, uint32_t *d_out, uint64_t out_capacity_words,
                                 uint64_t *d_chunk_bit_offset, uint64_t *d_total_bits, uint32_t *d_status,
                                 void *stream);
+
+/* ------------------------------------------------------------------------
+ * Batched encoding.  The paper encodes one field per call; the batch form
+ * (no paper counterpart) runs the histogram, codebook and encode stages of
+ * many independent fields as a handful of launches captured once in a CUDA
+ * graph: one histogram launch over all fields' tiles, one codebook launch
+ * with a CTA per field, a one-CTA planner that lays out every field's encode
+ * tiles from its codebook, and ONE persistent encode launch whose tiles run
+ * over all fields (each field keeps its own stream, offsets and look-back).
+ * Fields are grouped by dtype and alphabet class (<= 4,096 / <= 16,384 /
+ * larger), at most 512 per group; each group adds one such launch set.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    const void *d_sym;              /* n symbols of dtype, element aligned                            */
+    uint64_t n;                     /* < 2^32                                                         */
+    huff_dtype dtype;
+    uint32_t nbins;                 /* 1..65536 (<= 256 for HUFF_U8)                                  */
+    int32_t chunk_log2;             /* M, 4..30; -1 = chosen by the plan from {10, 12, 14}: size the
+                                       offsets for M = 10                                            */
+    uint32_t reserved;
+    uint32_t *d_out;                /* out_capacity_words uint32                                      */
+    uint64_t out_capacity_words;
+    uint64_t *d_chunk_bit_offset;   /* ceil(n / 2^M) + 1 uint64                                       */
+    uint64_t *d_total_bits;         /* one uint64                                                     */
+} huff_field;
+
+typedef struct {
+    int32_t autotune;       /* 1: time candidate settings on the fields at plan creation, keep the fastest */
+    int32_t reduce_log2;    /* r for every field, -1 = the Sec. IV-C rule on the group's mean codeword
+                               length (used when not tuning)                                            */
+    int32_t max_subtiles;   /* sub-tiles per encode tile, 1..8; 0 = 8 (used when not tuning)             */
+    int32_t ctas_per_sm;    /* encode CTAs per SM; 0 = as many as fit (used when not tuning)            */
+} huff_batch_cfg;
+
+typedef struct {
+    int32_t reduce_log2;     /* setting in use (-1 = rule)                                        */
+    int32_t max_subtiles;
+    int32_t ctas_per_sm;
+    int32_t chunk_log2;      /* M given to fields created with -1 (0: no such field)               */
+    uint32_t groups;         /* launch groups                                                     */
+    uint32_t kernels_per_run;/* kernel launches per huff_batch_encode                             */
+    uint32_t candidates;     /* settings timed by the tuner (0: not tuned)                        */
+    float tuned_ms;          /* best time of one batch during tuning                              */
+    uint64_t device_bytes;   /* device memory held by the plan                                    */
+} huff_batch_info;
+
+typedef struct huff_batch_plan huff_batch_plan;
+
+/* Default configuration: autotune off, r by rule, 8 sub-tiles, CTAs that fit. */
+void huff_batch_default_cfg(huff_batch_cfg *cfg);
+
+/*
+ * Builds a plan for nfields fields (1..65536).  The plan copies the records;
+ * their device buffers must stay valid while the plan is used, and their
+ * contents may change between runs.  It allocates its own device memory
+ * (histograms, codebooks, tile tables, look-back descriptors) and captures
+ * the launches in a CUDA graph.  With cfg->autotune it runs the batch for
+ * every candidate setting (outputs are the same for all of them) and keeps
+ * the fastest.  Work is done on `stream`, which is synchronised on return.
+ */
+huff_status huff_batch_plan_create(const huff_field *fields, uint32_t nfields, const huff_batch_cfg *cfg,
+                                   void *stream, huff_batch_plan **out);
+
+/* Runs the whole batch: one graph launch on `stream` (asynchronous). */
+huff_status huff_batch_encode(huff_batch_plan *plan, void *stream);
+
+/* Synchronises `stream` and copies each field's first device error (huff_status) into h_status[nfields]. */
+huff_status huff_batch_status(huff_batch_plan *plan, uint32_t *h_status, void *stream);
+
+huff_status huff_batch_get_info(const huff_batch_plan *plan, huff_batch_info *info);
+
+/* Device pointers of a field's codebook and histogram, owned by the plan (valid until destroy). */
+const void *huff_batch_codebook(const huff_batch_plan *plan, uint32_t field);
+const uint32_t *huff_batch_histogram(const huff_batch_plan *plan, uint32_t field);
+
+/* The M a field is encoded with (-1 for a bad field index). */
+int huff_batch_chunk_log2(const huff_batch_plan *plan, uint32_t field);
+
+/* Frees the plan after synchronising the device work it may still have in flight. */
+void huff_batch_plan_destroy(huff_batch_plan *plan);
 
 /* Synchronises `stream` and returns the first device error recorded in d_ws. */
 huff_status huff_get_status(const void *d_ws, void *stream);

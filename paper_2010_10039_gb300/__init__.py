@@ -40,6 +40,24 @@ class huff_params(ctypes.Structure):
                 ("block_threads", ctypes.c_int32), ("merge", ctypes.c_int32)]
 
 
+class huff_field(ctypes.Structure):
+    _fields_ = [("d_sym", ctypes.c_void_p), ("n", ctypes.c_uint64), ("dtype", ctypes.c_int32),
+                ("nbins", ctypes.c_uint32), ("chunk_log2", ctypes.c_int32), ("reserved", ctypes.c_uint32),
+                ("d_out", ctypes.c_void_p), ("out_capacity_words", ctypes.c_uint64),
+                ("d_chunk_bit_offset", ctypes.c_void_p), ("d_total_bits", ctypes.c_void_p)]
+
+
+class huff_batch_cfg(ctypes.Structure):
+    _fields_ = [("autotune", ctypes.c_int32), ("reduce_log2", ctypes.c_int32),
+                ("max_subtiles", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
+
+
+class huff_batch_info(ctypes.Structure):
+    _fields_ = [("reduce_log2", ctypes.c_int32), ("max_subtiles", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("chunk_log2", ctypes.c_int32), ("groups", ctypes.c_uint32), ("kernels_per_run", ctypes.c_uint32),
+                ("candidates", ctypes.c_uint32), ("tuned_ms", ctypes.c_float), ("device_bytes", ctypes.c_uint64)]
+
+
 _lib = None
 
 
@@ -68,6 +86,16 @@ def lib() -> ctypes.CDLL:
             "huff_get_status": (i32, [vp, vp]),
             "huff_status_string": (ctypes.c_char_p, [i32]),
             "huff_launch_count": (u64, []),
+            "huff_batch_default_cfg": (None, [ctypes.POINTER(huff_batch_cfg)]),
+            "huff_batch_plan_create": (i32, [ctypes.POINTER(huff_field), u32, ctypes.POINTER(huff_batch_cfg), vp,
+                                             ctypes.POINTER(vp)]),
+            "huff_batch_encode": (i32, [vp, vp]),
+            "huff_batch_status": (i32, [vp, ctypes.POINTER(u32), vp]),
+            "huff_batch_get_info": (i32, [vp, ctypes.POINTER(huff_batch_info)]),
+            "huff_batch_codebook": (vp, [vp, u32]),
+            "huff_batch_histogram": (vp, [vp, u32]),
+            "huff_batch_chunk_log2": (i32, [vp, u32]),
+            "huff_batch_plan_destroy": (None, [vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -267,3 +295,93 @@ class Pipeline:
 
     def status(self, stream=None) -> int:
         return huff_get_status(self.ws, stream)
+
+
+# ------------------------------------------------------------------ batched form
+
+class BatchPlan:
+    """huff_batch_plan over a list of fields.  Each field is a dict with
+    ``sym`` (1-D integer tensor on the device), ``nbins``, ``out`` (int32
+    tensor), ``offsets`` (int64 tensor), ``total_bits`` (int64 tensor of one
+    element) and optionally ``chunk_log2`` (default 10; -1 lets the plan
+    choose).  The tensors must outlive the plan."""
+
+    def __init__(self, fields, autotune: bool = False, reduce_log2: int = -1, max_subtiles: int = 0,
+                 ctas_per_sm: int = 0, stream=None):
+        self._keep = fields
+        self.n = len(fields)
+        arr = (huff_field * self.n)()
+        for i, f in enumerate(fields):
+            sym = f["sym"]
+            arr[i].d_sym = _ptr(sym)
+            arr[i].n = sym.numel()
+            arr[i].dtype = dtype_code(sym)
+            arr[i].nbins = int(f["nbins"])
+            arr[i].chunk_log2 = int(f.get("chunk_log2", 10))
+            arr[i].d_out = _ptr(f["out"])
+            arr[i].out_capacity_words = f["out"].numel()
+            arr[i].d_chunk_bit_offset = _ptr(f["offsets"])
+            arr[i].d_total_bits = _ptr(f["total_bits"])
+        cfg = huff_batch_cfg()
+        lib().huff_batch_default_cfg(ctypes.byref(cfg))
+        cfg.autotune = 1 if autotune else 0
+        cfg.reduce_log2 = reduce_log2
+        cfg.max_subtiles = max_subtiles
+        cfg.ctas_per_sm = ctas_per_sm
+        h = ctypes.c_void_p()
+        _check(lib().huff_batch_plan_create(arr, self.n, ctypes.byref(cfg), _stream(stream), ctypes.byref(h)),
+               "huff_batch_plan_create")
+        self.handle = h
+
+    def encode(self, stream=None) -> None:
+        _check(lib().huff_batch_encode(self.handle, _stream(stream)), "huff_batch_encode")
+
+    def status(self, stream=None) -> list[int]:
+        st = (ctypes.c_uint32 * self.n)()
+        _check(lib().huff_batch_status(self.handle, st, _stream(stream)), "huff_batch_status")
+        return list(st)
+
+    def info(self) -> dict:
+        inf = huff_batch_info()
+        _check(lib().huff_batch_get_info(self.handle, ctypes.byref(inf)), "huff_batch_get_info")
+        return {k: getattr(inf, k) for k, _ in huff_batch_info._fields_}
+
+    def codebook_ptr(self, i: int) -> int:
+        return lib().huff_batch_codebook(self.handle, i)
+
+    def histogram_ptr(self, i: int) -> int:
+        return lib().huff_batch_histogram(self.handle, i)
+
+    def chunk_log2(self, i: int) -> int:
+        return lib().huff_batch_chunk_log2(self.handle, i)
+
+    def codebook(self, i: int, nbins: int):
+        """Field i's codebook buffer (plan memory) as a device uint8 tensor view."""
+        return device_view(self.codebook_ptr(i), huff_codebook_bytes(nbins))
+
+    def histogram(self, i: int, nbins: int):
+        """Field i's histogram (plan memory) as a device int32 tensor view."""
+        return device_view(self.histogram_ptr(i), 4 * nbins).view(_torch().int32)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            lib().huff_batch_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _DeviceBytes:
+    def __init__(self, ptr: int, nbytes: int):
+        self.__cuda_array_interface__ = {"shape": (nbytes,), "typestr": "|u1", "data": (ptr, False), "version": 3}
+
+
+def device_view(ptr: int, nbytes: int):
+    """A uint8 torch tensor aliasing nbytes of library-owned device memory at ptr
+    (valid while the owner lives)."""
+    torch = _torch()
+    return torch.as_tensor(_DeviceBytes(ptr, nbytes), device="cuda")

@@ -61,7 +61,7 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     if jobs:
         with ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
             list(ex.map(run, jobs))
-    if jobs or not os.path.exists(LIB):
+    if jobs or not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
         tmp = LIB + f".tmp{os.getpid()}"
         run([nvcc, "-shared"] + ARCH + ["-o", tmp] + objs + ["-lpthread"])
         os.replace(tmp, LIB)

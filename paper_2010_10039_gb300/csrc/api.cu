@@ -3,24 +3,25 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <mutex>
+#include <map>
+#include <utility>
 
-#include "common.cuh"
+#include "kernels.cuh"
 
 namespace huff {
 
-huff_status histogram_launch(const void *, uint64_t, huff_dtype, uint32_t, uint32_t *, uint32_t *, cudaStream_t);
-huff_status codebook_launch(const uint32_t *, uint32_t, void *, uint8_t *, uint32_t *, cudaStream_t);
-size_t codebook_scratch_bytes(uint32_t nbins);
-huff_status encode_launch(const void *, uint64_t, huff_dtype, const void *, uint32_t, int, int, uint32_t *, uint64_t,
-                          uint64_t *, uint64_t *, uint8_t *, uint32_t *, cudaStream_t);
-size_t encode_scratch_bytes(uint64_t n);
-int encode_run_log2(huff_dtype dtype);
-huff_status decode_launch(const uint32_t *, uint64_t, const uint64_t *, int, uint64_t, huff_dtype, const void *,
-                          uint32_t, void *, uint32_t *, cudaStream_t);
-
 static std::atomic<uint64_t> g_launches{0};
 
-void note_launch(int k) { g_launches.fetch_add((uint64_t)k, std::memory_order_relaxed); }
+// Launches enqueued while a graph is being captured run only when the graph
+// runs; the capturing thread turns counting off and the graph launch counts them.
+static thread_local bool t_count_off = false;
+
+void launch_count_suppress(bool on) { t_count_off = on; }
+
+void note_launch(int k) {
+    if (!t_count_off) g_launches.fetch_add((uint64_t)k, std::memory_order_relaxed);
+}
 
 int sm_count() {
     static int cached[64] = {0};
@@ -35,6 +36,27 @@ int sm_count() {
     return cached[dev];
 }
 
+bool allow_dynamic_smem(const void *func, size_t need) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, int> limit;   // dynamic bytes allowed per (device, kernel)
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = limit.find({dev, func});
+    if (it == limit.end()) {
+        int optin = 0;
+        if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || optin <= 0)
+            return false;
+        // static shared memory of the kernel counts against the same maximum
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, func) != cudaSuccess || fa.sharedSizeBytes > (size_t)optin) return false;
+        const int lim = optin - (int)fa.sharedSizeBytes;
+        if (cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess) return false;
+        it = limit.emplace(std::make_pair(dev, func), lim).first;
+    }
+    return need <= (size_t)it->second;
+}
+
 static bool dtype_ok(huff_dtype d) { return d == HUFF_U8 || d == HUFF_U16 || d == HUFF_U32; }
 
 static bool nbins_ok(huff_dtype d, uint32_t nbins) {
@@ -42,6 +64,9 @@ static bool nbins_ok(huff_dtype d, uint32_t nbins) {
     if (d == HUFF_U8 && nbins > 256) return false;
     return true;
 }
+
+// Typed device arrays must be aligned to their element size.
+static bool elem_aligned(const void *p, huff_dtype d) { return ((uintptr_t)p % (uintptr_t)d) == 0; }
 
 static uint32_t *status_of(void *ws) { return static_cast<uint32_t *>(ws); }
 static uint8_t *scratch_of(void *ws) { return static_cast<uint8_t *>(ws) + kWsHeaderBytes; }
@@ -94,6 +119,7 @@ huff_status huff_histogram(const void *d_sym, uint64_t n, huff_dtype dtype, uint
                            void *d_ws, void *stream) {
     if (!dtype_ok(dtype) || !nbins_ok(dtype, nbins) || !d_hist || !d_ws || (n && !d_sym) || n >= (1ull << 32))
         return HUFF_ERR_INVALID_ARG;
+    if (!elem_aligned(d_sym, dtype) || ((uintptr_t)d_hist & 3) != 0) return HUFF_ERR_INVALID_ARG;
     return histogram_launch(d_sym, n, dtype, nbins, d_hist, status_of(d_ws), (cudaStream_t)stream);
 }
 
@@ -113,6 +139,9 @@ huff_status huff_encode(const void *d_sym, uint64_t n, huff_dtype dtype, const v
         !d_ws || (n && (!d_sym || !d_out)) || n >= (1ull << 32))
         return HUFF_ERR_INVALID_ARG;
     if (((uintptr_t)d_codebook & 15) != 0) return HUFF_ERR_INVALID_ARG;
+    if (!elem_aligned(d_sym, dtype) || ((uintptr_t)d_out & 3) != 0 || ((uintptr_t)d_chunk_bit_offset & 7) != 0 ||
+        ((uintptr_t)d_total_bits & 7) != 0)
+        return HUFF_ERR_INVALID_ARG;
     if (prm.chunk_log2 < 4 || prm.chunk_log2 > 30 || prm.chunk_log2 < encode_run_log2(dtype)) return HUFF_ERR_INVALID_ARG;
     if (prm.reduce_log2 != -1 && (prm.reduce_log2 < 0 || prm.reduce_log2 > prm.chunk_log2)) return HUFF_ERR_INVALID_ARG;
     if (prm.merge < HUFF_MERGE_AUTO || prm.merge > HUFF_MERGE_SHUFFLE) return HUFF_ERR_INVALID_ARG;
@@ -132,6 +161,9 @@ huff_status huff_decode(const uint32_t *d_in, uint64_t total_bits, const uint64_
     if (!dtype_ok(dtype) || !nbins_ok(dtype, nbins) || !d_codebook || !d_ws || (n && (!d_in || !d_out || !d_chunk_bit_offset)))
         return HUFF_ERR_INVALID_ARG;
     if (chunk_log2 < 0 || chunk_log2 > 30) return HUFF_ERR_INVALID_ARG;
+    if (!elem_aligned(d_out, dtype) || ((uintptr_t)d_in & 3) != 0 || ((uintptr_t)d_chunk_bit_offset & 7) != 0 ||
+        ((uintptr_t)d_codebook & 15) != 0)
+        return HUFF_ERR_INVALID_ARG;
     return decode_launch(d_in, total_bits, d_chunk_bit_offset, chunk_log2, n, dtype, d_codebook, nbins, d_out,
                          status_of(d_ws), (cudaStream_t)stream);
 }

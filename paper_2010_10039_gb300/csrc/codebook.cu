@@ -32,20 +32,12 @@
 // one length are consecutive in ascending symbol id (a warp-match rank inside
 // each 1024-id slice plus a per-length running base).  Entry and the
 // (length, id)-sorted symbol list form the reverse codebook.
-#include "common.cuh"
+#include "kernels.cuh"
 
 namespace huff {
 
 constexpr int kCbThreads = 1024;
 constexpr uint32_t kCbSmemBins = 4096;     // arrays live in shared memory up to this alphabet
-
-struct CbArgs {
-    const uint32_t *hist;
-    uint32_t nbins;
-    uint8_t *book;         // codebook buffer
-    uint8_t *scratch;      // global scratch (large alphabets)
-    uint32_t *status;
-};
 
 struct CbArrays {
     uint64_t *keys;     // P       sort keys (count << 16 | id), unused = ~0
@@ -116,8 +108,9 @@ __device__ __forceinline__ uint32_t count_below(const uint32_t *w, uint32_t lo, 
     return a - lo;
 }
 
-__global__ void __launch_bounds__(kCbThreads) codebook_kernel(CbArgs g) {
-    extern __shared__ __align__(16) uint8_t smem[];
+// Builds the codebook of one histogram with the whole CTA; `arrays` holds the
+// construction's arrays (shared memory for small alphabets).
+__device__ void codebook_body(const CbArgs &g, uint8_t *arrays) {
     __shared__ uint64_t s_sum, s_tbits;
     __shared__ uint32_t s_m, s_c, s_ih, s_it, s_mL, s_mI, s_rounds, s_maxlen, s_bad;
     __shared__ uint32_t s_count[HUFF_MAX_LEN + 1];
@@ -129,7 +122,7 @@ __global__ void __launch_bounds__(kCbThreads) codebook_kernel(CbArgs g) {
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t nbins = g.nbins;
     const uint32_t P = pow2_ceil(nbins);
-    CbArrays A = cb_carve(nbins <= kCbSmemBins ? smem : g.scratch, nbins);
+    CbArrays A = cb_carve(arrays, nbins);
     huff_codebook_header *hdr = reinterpret_cast<huff_codebook_header *>(g.book);
     uint64_t *cw = reinterpret_cast<uint64_t *>(g.book + cb_cw_offset());
     uint32_t *sorted_syms = reinterpret_cast<uint32_t *>(g.book + cb_sorted_offset(nbins));
@@ -330,6 +323,46 @@ __global__ void __launch_bounds__(kCbThreads) codebook_kernel(CbArgs g) {
     }
 }
 
+__global__ void __launch_bounds__(kCbThreads) codebook_kernel(CbArgs g) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    codebook_body(g, g.nbins <= kCbSmemBins ? smem : g.scratch);
+}
+
+// Codebooks of a batch: CTA b builds those of fields b, b + grid, ...;
+// alphabets above the shared-memory limit use scratch + b * scratch_stride.
+__global__ void __launch_bounds__(kCbThreads) codebook_batch_kernel(const CbArgs *gs, uint32_t nfields,
+                                                                     uint8_t *scratch, size_t scratch_stride) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    for (uint32_t f = blockIdx.x; f < nfields; f += gridDim.x) {
+        const CbArgs g = gs[f];
+        codebook_body(g, g.nbins <= kCbSmemBins ? smem : scratch + blockIdx.x * scratch_stride);
+        __syncthreads();     // the next field reuses the shared state
+    }
+}
+
+size_t codebook_array_bytes(uint32_t nbins) { return cb_array_bytes(nbins); }
+
+// Shared memory a batched codebook launch needs when its largest alphabet is max_nbins.
+size_t codebook_batch_smem(uint32_t max_nbins) { return max_nbins <= kCbSmemBins ? cb_array_bytes(max_nbins) : 0; }
+
+huff_status codebook_batch_prepare(uint32_t max_nbins, int *ctas_per_sm) {
+    const size_t smem = codebook_batch_smem(max_nbins);
+    if (!allow_dynamic_smem((const void *)codebook_batch_kernel, smem))
+        return HUFF_ERR_CUDA;
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, codebook_batch_kernel, kCbThreads, smem);
+    *ctas_per_sm = occ < 1 ? 1 : occ;
+    return HUFF_OK;
+}
+
+huff_status codebook_batch_launch(const CbArgs *d_args, uint32_t nfields, uint32_t max_nbins, uint32_t grid,
+                                  uint8_t *scratch, size_t scratch_stride, cudaStream_t st) {
+    codebook_batch_kernel<<<grid, kCbThreads, codebook_batch_smem(max_nbins), st>>>(d_args, nfields, scratch,
+                                                                                     scratch_stride);
+    note_launch();
+    return cudaGetLastError() == cudaSuccess ? HUFF_OK : HUFF_ERR_CUDA;
+}
+
 size_t codebook_scratch_bytes(uint32_t nbins) {
     return nbins <= kCbSmemBins ? 0 : cb_array_bytes(nbins);
 }
@@ -343,7 +376,7 @@ huff_status codebook_launch(const uint32_t *d_hist, uint32_t nbins, void *d_code
     a.scratch = scratch;
     a.status = status;
     size_t smem = nbins <= kCbSmemBins ? cb_array_bytes(nbins) : 0;
-    if (cudaFuncSetAttribute(codebook_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    if (!allow_dynamic_smem((const void *)codebook_kernel, smem))
         return HUFF_ERR_CUDA;
     codebook_kernel<<<1, kCbThreads, smem, st>>>(a);
     note_launch();

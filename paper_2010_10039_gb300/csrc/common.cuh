@@ -122,6 +122,12 @@ __device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
 // ---------------------------------------------------------------- host-side helpers
 
 int sm_count();                       // cached multiprocessor count of the current device
+// Lets `func` use up to the device's opt-in maximum of dynamic shared memory
+// (once per function and device).  The limit is never lowered again, so
+// launches of the same kernel with different sizes -- from other threads,
+// other plans or captured graphs -- cannot invalidate each other; false if
+// `need` is above the maximum or the call failed.
+bool allow_dynamic_smem(const void *func, size_t need);
 void note_launch(int k = 1);          // launch counter for huff_launch_count()
 
 }  // namespace huff

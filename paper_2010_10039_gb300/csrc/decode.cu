@@ -3,7 +3,7 @@
 // sorted_syms[Entry[l] + v - First[l]].  The chunk offsets written by the
 // encoder let every chunk be decoded independently: one thread per chunk,
 // reading the stream through a 64-bit window.
-#include "common.cuh"
+#include "kernels.cuh"
 
 namespace huff {
 

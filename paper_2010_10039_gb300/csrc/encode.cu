@@ -1,806 +1,9 @@
-// Encoding (Sec. IV-C) fused with the gathering of Table I ("get blockwise
-// code len" prefix sum and "coalescing copy") into one persistent kernel.
-//
-// Paper design (V100): a chunk of N = 2^M symbols is reduce-merged (each
-// thread concatenates 2^r codewords in a register: Merge((a,l)_{2k},
-// (a,l)_{2k+1}) = (a_{2k} (+) a_{2k+1}, l_{2k} + l_{2k+1})) and then
-// shuffle-merged in shared memory for s = M - r log steps until the chunk is
-// one dense run of words; a prefix sum over chunk lengths and a copy then
-// gather the chunks into one stream.
-//
-// GB300 form (this file):
-//  * sub-tiles of 4096 (u16) symbols are fetched by the bulk-copy engine into
-//    a ring of shared-memory stages (cp.async.bulk + mbarrier); tile ids come
-//    from an atomic counter, so tiles start in stream order;
-//  * reduce-merge: each thread looks up 2^r codewords in a shared-memory
-//    codebook and concatenates them in a 64-bit register; r follows the
-//    paper's rule from the average codeword length;
-//  * the s log steps of shuffle-merge become one exclusive scan of the merged
-//    lengths (a warp scan plus a block-level sum of 8 warp totals), after
-//    which every merged run is placed once into a shared-memory bit ring: one
-//    data movement instead of s;
-//  * the tile's stream offset comes from a decoupled look-back (Merrill &
-//    Garland) run by a dedicated warp while the merge warps go on; every tile
-//    publishes its length together with its last 32 bits, so a tile writes the
-//    word it shares with its predecessor whole: the dense stream is written
-//    once, with coalesced plain stores by a dedicated write-out warp, no
-//    pre-zeroing and no global atomics, bit-identical to serial packing.
-#include "common.cuh"
+// Single-field encode launch (huff_encode, huff_encode_noalloc): the kernel
+// of encode_impl.cuh over one field whose codebook-derived tile layout the
+// kernel works out itself.
+#include "encode_impl.cuh"
 
 namespace huff {
-
-constexpr int kEncThreads = 256;           // merge threads (8 warps)
-constexpr int kEncRPT = 2;                 // consecutive 16-byte vectors per merge thread per sub-tile
-constexpr int kEncStages = 4;              // sub-tile stages in flight
-constexpr int kEncVecBytes = 16;
-constexpr int kEncSubBytes = kEncThreads * kEncRPT * kEncVecBytes;   // 8 KB per sub-tile
-constexpr int kEncMaxSubs = 8;             // sub-tiles per tile (fewer when codewords are long)
-constexpr int kEncMaxLen = 48;             // longest codeword the bit ring is sized for
-constexpr int kSlots = 4;                  // tiles between merge and write-out
-constexpr uint32_t kEncSmemTableBins = 4096;
-constexpr uint64_t kFlagAgg = 1ull << 62;
-constexpr uint64_t kFlagPre = 2ull << 62;
-constexpr uint64_t kValMask = (1ull << 62) - 1;
-constexpr uint64_t kAggLenMask = (1ull << 24) - 1;
-constexpr uint32_t kBad32 = 1u << 23;      // u32 table entry flag: symbol without codeword
-constexpr int kEncCtaThreads = kEncThreads + 64;   // merge warps + look-back warp + write-out warp
-
-struct EncArgs {
-    const uint8_t *sym;
-    uint64_t n;
-    uint64_t nchunks;
-    const uint8_t *book;
-    uint32_t *out;
-    uint64_t cap_words;
-    uint64_t *offs;
-    uint64_t *total_bits;
-    uint32_t *tile_counter;
-    uint64_t *desc;          // look-back descriptor per tile: {aggregate word, prefix word}
-    uint32_t *status;
-    int chunk_log2;
-    int aligned;             // input is 16-byte aligned: full sub-tiles use bulk copies
-    uint32_t nbins;          // alphabet size the caller sized shared memory for
-    uint64_t max_tiles;      // descriptors available (one sub-tile per tile)
-    int reduce_log2;         // r, or -1 for the average-length rule
-};
-
-template <typename Sym>
-struct VecOf {
-    static constexpr int N = kEncVecBytes / sizeof(Sym);   // symbols per 16-byte vector
-};
-
-template <typename Sym>
-__host__ __device__ constexpr uint32_t enc_sub_syms() { return kEncThreads * kEncRPT * VecOf<Sym>::N; }
-
-// Ring of merged bits: 64 KB for u8 sub-tiles (8192 symbols), 32 KB otherwise;
-// always large enough for one sub-tile of kEncMaxLen-bit codewords.
-template <typename Sym>
-__host__ __device__ constexpr uint32_t ring_words() { return sizeof(Sym) == 1 ? 16384u : 8192u; }
-
-// sub-tiles per tile: the tile's worst case (every codeword max_len bits)
-// must fit the ring on its own
-template <typename Sym>
-__host__ __device__ inline uint32_t enc_subs_per_tile(uint32_t max_len) {
-    uint32_t m = max_len ? max_len : 1;
-    uint32_t k = (ring_words<Sym>() - 64) * 32u / (enc_sub_syms<Sym>() * m);
-    return k < 1 ? 1 : (k > kEncMaxSubs ? kEncMaxSubs : k);
-}
-
-__device__ __forceinline__ void sym_from_vec(const uint4 &v, uint32_t *s, uint8_t) {
-    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-    for (int j = 0; j < 16; j++) s[j] = (w[j >> 2] >> (8 * (j & 3))) & 0xFFu;
-}
-__device__ __forceinline__ void sym_from_vec(const uint4 &v, uint32_t *s, uint16_t) {
-    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-    for (int j = 0; j < 8; j++) s[j] = (j & 1) ? (w[j >> 1] >> 16) : (w[j >> 1] & 0xFFFFu);
-}
-__device__ __forceinline__ void sym_from_vec(const uint4 &v, uint32_t *s, uint32_t) {
-    s[0] = v.x; s[1] = v.y; s[2] = v.z; s[3] = v.w;
-}
-
-// ---------------------------------------------------------------- codebook entries
-// u32 form (codewords up to 23 bits): len << 24 | code, kBad32 for no codeword.
-// u64 form: the codebook's cw (len << 58 | code), 0 for no codeword.
-
-template <typename Entry>
-__device__ __forceinline__ Entry entry_from_cw(uint64_t c);
-template <>
-__device__ __forceinline__ uint32_t entry_from_cw<uint32_t>(uint64_t c) {
-    uint32_t l = (uint32_t)(c >> HUFF_CW_LEN_SHIFT);
-    return l ? ((l << 24) | (uint32_t)(c & 0x7FFFFFu)) : kBad32;
-}
-template <>
-__device__ __forceinline__ uint64_t entry_from_cw<uint64_t>(uint64_t c) { return c; }
-
-template <typename Entry>
-__device__ __forceinline__ uint32_t ent_len(Entry e);
-template <>
-__device__ __forceinline__ uint32_t ent_len<uint32_t>(uint32_t e) { return e >> 24; }
-template <>
-__device__ __forceinline__ uint32_t ent_len<uint64_t>(uint64_t e) { return (uint32_t)(e >> HUFF_CW_LEN_SHIFT); }
-
-template <typename Entry>
-__device__ __forceinline__ uint64_t ent_code(Entry e);
-template <>
-__device__ __forceinline__ uint64_t ent_code<uint32_t>(uint32_t e) { return e & 0x7FFFFFu; }
-template <>
-__device__ __forceinline__ uint64_t ent_code<uint64_t>(uint64_t e) { return e & ((1ull << HUFF_CW_LEN_SHIFT) - 1); }
-
-// Entry of symbol s.  The shared-memory table has a power-of-two number of
-// slots (tmask + 1 >= nbins, slots past nbins have no codeword) and is indexed
-// with s & tmask; a symbol beyond the table is caught by the vector range test.
-// The global table (large alphabets) is read only for s < nbins.
-template <typename Entry, bool GTAB>
-__device__ __forceinline__ Entry table_get(const Entry *tab, const uint64_t *gcw, uint32_t s, uint32_t nbins,
-                                           uint32_t tmask) {
-    if (GTAB) {
-        uint64_t c = s < nbins ? __ldg(gcw + s) : 0ull;
-        return entry_from_cw<Entry>(c);
-    } else {
-        return tab[s & tmask];
-    }
-}
-
-// True when some symbol of the vector is beyond a table of tmask + 1 slots.
-__device__ __forceinline__ bool vec_out_of_table(const uint4 &v, uint32_t tmask, uint8_t) {
-    const uint32_t m = tmask * 0x01010101u;
-    return ((v.x | v.y | v.z | v.w) & ~m) != 0;
-}
-__device__ __forceinline__ bool vec_out_of_table(const uint4 &v, uint32_t tmask, uint16_t) {
-    const uint32_t m = tmask | (tmask << 16);
-    return ((v.x | v.y | v.z | v.w) & ~m) != 0;
-}
-__device__ __forceinline__ bool vec_out_of_table(const uint4 &v, uint32_t tmask, uint32_t) {
-    return ((v.x | v.y | v.z | v.w) & ~tmask) != 0;
-}
-
-// acc = acc (+) codeword: append l bits (one step of reduce-merge).
-template <typename Entry>
-__device__ __forceinline__ void concat(uint64_t &acc, Entry e, uint32_t l) {
-    if (sizeof(Entry) == 4) {
-        // l <= 23: a 32-bit funnel shift makes the high word, no 64-bit shift
-        uint32_t lo = (uint32_t)acc, hi = (uint32_t)(acc >> 32);
-        hi = __funnelshift_l(lo, hi, l);
-        lo = (lo << l) | (uint32_t)ent_code<Entry>(e);
-        acc = ((uint64_t)hi << 32) | lo;
-    } else {
-        acc = (acc << l) | ent_code<Entry>(e);
-    }
-}
-
-// ---------------------------------------------------------------- bit ring
-
-// Appends codewords one by one (runs longer than 64 bits); completed words go
-// to the ring at word base + (bit position >> 5).
-template <uint32_t RMASK>
-struct BitSink {
-    uint64_t acc;
-    uint32_t nacc;     // valid low bits of acc (current word so far)
-    uint32_t wi;       // word index being filled (not yet masked)
-    uint32_t lead;     // placeholder bits of earlier runs in the first word
-    uint32_t *buf;
-
-    __device__ __forceinline__ void begin(uint32_t *b, uint32_t base, uint32_t pos) {
-        buf = b; wi = base + (pos >> 5); nacc = pos & 31; lead = nacc; acc = 0;
-    }
-    __device__ __forceinline__ void put(uint32_t c, uint32_t l) {
-        acc = (acc << l) | c;
-        nacc += l;
-        if (nacc >= 32) {
-            nacc -= 32;
-            uint32_t w = (uint32_t)(acc >> nacc);
-            if (lead) atomicOr(&buf[wi & RMASK], w); else buf[wi & RMASK] = w;
-            lead = 0;
-            wi++;
-        }
-    }
-    __device__ __forceinline__ void put64(uint64_t c, uint32_t l) {
-        if (l > 32) { put((uint32_t)(c >> 32), l - 32); put((uint32_t)c, 32); }
-        else put((uint32_t)c, l);
-    }
-    __device__ __forceinline__ void end() {
-        if (nacc > lead) atomicOr(&buf[wi & RMASK], (uint32_t)(acc << (32 - nacc)));
-    }
-};
-
-// Places a merged run of rb (1..64) bits, right-aligned in acc, at tile bit
-// pos of a tile that starts at ring word base: at most three words, combined
-// with shared-memory OR (the first and last are shared with neighbouring runs).
-template <uint32_t RMASK>
-__device__ __forceinline__ void place_run(uint32_t *ring, uint32_t base, uint32_t pos, uint64_t acc, uint32_t rb) {
-    const uint32_t lo = (uint32_t)acc, hi = (uint32_t)(acc >> 32);
-    // MSB-align the run in (ah:al)
-    const uint32_t u = 64 - rb;                          // 0..63
-    const uint32_t ah = u < 32 ? __funnelshift_l(lo, hi, u) : lo << (u - 32);
-    const uint32_t al = u < 32 ? lo << u : 0u;
-    // shift right by the bit offset inside the first word: three frame words
-    const uint32_t sh = pos & 31, w = base + (pos >> 5);
-    const uint32_t f0 = ah >> sh;
-    const uint32_t f1 = __funnelshift_r(al, ah, sh);
-    const uint32_t f2 = __funnelshift_r(0u, al, sh);
-    if (f0) atomicOr(&ring[w & RMASK], f0);
-    if (f1) atomicOr(&ring[(w + 1) & RMASK], f1);
-    if (f2) atomicOr(&ring[(w + 2) & RMASK], f2);
-}
-
-// ---------------------------------------------------------------- look-back descriptors
-// 16 bytes per tile, zeroed before the launch:
-//   agg = kFlagAgg | last32 << 24 | L    the tile's length and last 32 stream bits
-//   pre = kFlagPre | (offset + L)        its inclusive stream offset
-// Each word carries everything a reader needs from it, so both are written
-// and read with plain (relaxed) 64-bit accesses and no fences.
-
-__device__ __forceinline__ void ld_desc(const uint64_t *d, uint64_t &agg, uint64_t &pre) {
-    asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(agg), "=l"(pre) : "l"(d) : "memory");
-}
-__device__ __forceinline__ void st_relaxed_u64(uint64_t *p, uint64_t v) {
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t *p) {
-    uint64_t v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// Decoupled look-back by one warp, 128 predecessor descriptors per step:
-// returns the exclusive stream offset of tile j (length L) and, in lane 0,
-// the previous tile's last 32 bits; publishes tile j's inclusive offset.
-__device__ uint64_t lookback_warp(const EncArgs &a, uint64_t j, uint64_t L, uint32_t *prev_tail) {
-    const uint32_t lane = threadIdx.x & 31;
-    uint64_t excl = 0;
-    int64_t base = (int64_t)j;                 // look at tiles [base-128, base)
-    uint32_t spins = 0, nap = 32;
-    for (;;) {
-        uint64_t v[4];
-        uint32_t pkey = 0xFFFFFFFFu, zkey = 0xFFFFFFFFu;
-#pragma unroll
-        for (int q = 3; q >= 0; q--) {
-            const int64_t idx = base - 1 - (int64_t)(4 * lane + q);
-            uint64_t agg = 0, pre = kFlagPre;       // before tile 0: prefix 0
-            if (idx >= 0) ld_desc(&a.desc[2 * idx], agg, pre);
-            if (pre) { pkey = 4 * lane + q; v[q] = pre & kValMask; }
-            else { v[q] = agg & kAggLenMask; if (!agg) zkey = 4 * lane + q; }
-        }
-        uint32_t pnear = pkey, znear = zkey;
-#pragma unroll
-        for (int o = 16; o; o >>= 1) {
-            pnear = min(pnear, __shfl_xor_sync(0xFFFFFFFFu, pnear, o));
-            znear = min(znear, __shfl_xor_sync(0xFFFFFFFFu, znear, o));
-        }
-        if (znear < pnear) {                   // a closer tile has not published yet
-            if (++spins > kSpinLimit) {
-                if (lane == 0) set_error(a.status, HUFF_ERR_TIMEOUT);
-                break;
-            }
-            __nanosleep(nap);                  // back off: polling competes with the merge warps
-            nap = nap < 1024 ? 2 * nap : 1024;
-            continue;
-        }
-        uint64_t part = 0;
-#pragma unroll
-        for (int q = 0; q < 4; q++)
-            if (4 * lane + q <= pnear) part += v[q];
-#pragma unroll
-        for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, o);
-        excl += part;
-        if (pnear != 0xFFFFFFFFu) break;
-        base -= 128;
-    }
-    if (lane == 0) {
-        st_relaxed_u64(&a.desc[2 * j + 1], kFlagPre | (excl + L));
-        // the previous tile's last 32 bits travel in its aggregate word
-        uint64_t agg = 0;
-        for (uint32_t sp = 0; sp < kSpinLimit; sp++) {
-            agg = ld_relaxed_u64(&a.desc[2 * (j - 1)]);
-            if (agg) break;
-        }
-        if (!agg) set_error(a.status, HUFF_ERR_TIMEOUT);
-        *prev_tail = (uint32_t)(agg >> 24);
-    }
-    return excl;
-}
-
-// ---------------------------------------------------------------- input ring
-
-// Producer of the bulk-copy ring (merge thread 0 only).  Sub-tiles are fetched
-// in stream order; a new tile id is taken once every sub-tile of the current
-// tile is under way.
-struct Producer {
-    uint64_t tile;      // tile being fetched
-    uint64_t next;      // id of the tile after it (taken one tile ahead, so its latency is hidden)
-    uint32_t sub;       // next sub-tile of it to fetch
-    uint32_t slot;      // next ring slot
-};
-
-template <typename Sym>
-__device__ __forceinline__ void produce_next(const EncArgs &a, Producer &p, uint32_t nsub, uint64_t ntiles,
-                                             uint8_t *stage, uint64_t *bars, volatile uint64_t *s_stage_tile) {
-    constexpr uint32_t SUB = enc_sub_syms<Sym>();
-    if (p.sub >= nsub && p.tile < ntiles) {
-        p.tile = p.next;
-        p.next = p.tile < ntiles ? atomicAdd(a.tile_counter, 1u) : p.tile;
-        p.sub = 0;
-    }
-    const int s = (int)(p.slot % kEncStages);
-    s_stage_tile[s] = p.tile;
-    if (p.tile < ntiles) {
-        uint64_t t0 = (p.tile * nsub + p.sub) * (uint64_t)SUB;
-        if (a.aligned && t0 + SUB <= a.n) {
-            mbar_arrive_expect_tx(&bars[s], kEncSubBytes);
-            bulk_g2s(stage + s * kEncSubBytes, a.sym + t0 * sizeof(Sym), kEncSubBytes, &bars[s]);
-        } else {
-            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bars[s])) : "memory");
-        }
-    }
-    p.sub++;
-    p.slot++;
-}
-
-__device__ __forceinline__ void merge_sync() {       // the 8 merge warps only
-    asm volatile("bar.sync 1, %0;" ::"n"(kEncThreads) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-// A tile between merge and write-out.
-struct TileSlot {
-    uint64_t tile;        // tile id (>= ntiles: no more tiles)
-    uint64_t G;           // exclusive stream offset
-    uint32_t L;           // length in bits
-    uint32_t base;        // first ring word (running counter, masked on use)
-    uint32_t prev;        // last 32 bits of the tile before it
-    uint32_t pad;
-};
-
-struct EncShared {
-    uint64_t bars[kEncStages];      // sub-tile stages (bulk copies)
-    uint64_t full[kSlots];          // merge -> look-back: tile merged and its aggregate published
-    uint64_t gready[kSlots];        // look-back -> write-out: offset known
-    uint64_t sfree[kSlots];         // write-out -> merge: slot reusable
-    uint64_t stage_tile[kEncStages];
-    TileSlot slot[kSlots];
-    uint32_t ring_tail;             // ring words before this counter are free again
-    uint32_t wsum[2][kEncThreads / 32];   // warp totals of the merged lengths (double-buffered)
-};
-
-// ---------------------------------------------------------------- merge warps
-
-// Reduce-merge of one 16-byte vector: 2^R2 codewords per run, concatenated
-// in a 64-bit register.  FULL: all symbols valid and below nbins.  `bad`
-// collects kBad32 when a valid position has no codeword.
-template <typename Sym, typename Entry, bool GTAB, int R2, bool FULL>
-__device__ __forceinline__ uint32_t merge_vec(const uint32_t *sv, uint32_t valid, const Entry *tab,
-                                              const uint64_t *gcw, uint32_t nbins, uint32_t tmask, uint64_t *acc,
-                                              uint32_t *rb, uint32_t &bad) {
-    constexpr int V = VecOf<Sym>::N;
-    constexpr int RL = 1 << R2;
-    constexpr int NR = V / RL;
-    uint32_t tot = 0;
-#pragma unroll
-    for (int r = 0; r < NR; r++) {
-        uint64_t ac = 0;
-        uint32_t bb = 0;
-#pragma unroll
-        for (int x = 0; x < RL; x++) {
-            const int xi = r * RL + x;
-            Entry en = table_get<Entry, GTAB>(tab, gcw, sv[xi], nbins, tmask);
-            if (!FULL && xi >= (int)valid) en = (Entry)0;            // padding past n: length 0
-            else if (sizeof(Entry) == 4) bad |= (uint32_t)en;
-            else bad |= en == 0 ? kBad32 : 0u;
-            const uint32_t l = ent_len<Entry>(en);
-            concat<Entry>(ac, en, l);
-            bb += l;
-        }
-        acc[r] = ac;
-        rb[r] = bb;
-        tot += bb;
-    }
-    return tot;
-}
-
-// The 8 merge warps: reduce-merge every tile into the bit ring, publish its
-// aggregate and hand it to the look-back and write-out warps.  R2 = r:
-// 2^r codewords per register.
-template <typename Sym, typename Entry, bool GTAB, int R2>
-__device__ void merge_warps(const EncArgs &a, uint8_t *stage, uint32_t *ring, const Entry *tab, uint32_t nbins,
-                            uint32_t tmask, uint32_t nsub, uint32_t max_len, EncShared &S) {
-    constexpr int V = VecOf<Sym>::N;              // symbols per 16-byte vector
-    constexpr int RL = 1 << R2;                   // symbols per merged run
-    constexpr int NR = V / RL;                    // runs per vector
-    static_assert(RL <= V, "a run stays inside one vector");
-    constexpr uint32_t SUB = enc_sub_syms<Sym>();
-    constexpr uint32_t RW = ring_words<Sym>();
-    constexpr uint32_t RMASK = RW - 1;
-    const uint32_t TILE = SUB * nsub;
-    const uint64_t ntiles = (a.n + TILE - 1) / TILE;
-    const uint64_t *gcw = reinterpret_cast<const uint64_t *>(a.book + cb_cw_offset());
-    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int M = a.chunk_log2;
-    const uint64_t chunk_mask = (1ull << M) - 1;
-    volatile uint64_t *stage_tile = S.stage_tile;
-    volatile uint32_t *ring_tail = &S.ring_tail;
-    // chunks of at most a sub-tile start at vectors q with q % vpc == 0 (vpc a power of two)
-    const bool small_chunks = (1ull << M) <= SUB;
-    const uint32_t vpc = small_chunks ? (uint32_t)((1ull << M) / V) : 1u;
-    // words one sub-tile can need at most
-    const uint32_t sub_words = (SUB * max_len + 31) / 32 + 2;
-
-    Producer prod;
-    prod.slot = 0;
-    prod.sub = nsub;
-    prod.tile = 0;
-    prod.next = 0;
-    if (tid == 0) {
-        prod.next = atomicAdd(a.tile_counter, 1u);
-        for (int i = 0; i < kEncStages; i++) produce_next<Sym>(a, prod, nsub, ntiles, stage, S.bars, stage_tile);
-    }
-    merge_sync();
-
-    uint32_t it = 0, t = 0, base = 0;
-    for (;; t++) {
-        const uint64_t j = stage_tile[it % kEncStages];
-        const uint32_t sl = t % kSlots;
-        if (t >= kSlots && !mbar_wait_bounded(&S.sfree[sl], ((t / kSlots) - 1) & 1))
-            set_error(a.status, HUFF_ERR_TIMEOUT);
-        if (j >= ntiles) {
-            if (tid == 0) {
-                S.slot[sl].tile = ~0ull;
-                mbar_arrive(&S.full[sl]);
-            }
-            break;
-        }
-        const uint64_t t0 = j * (uint64_t)TILE;
-        uint32_t running = 0;
-
-        for (uint32_t sub = 0; sub < nsub; sub++, it++) {
-            const int s = (int)(it % kEncStages);
-            const uint32_t parity = (it / kEncStages) & 1;
-            const uint64_t s0 = t0 + (uint64_t)sub * SUB;
-            const bool full = a.aligned && s0 + SUB <= a.n;
-            if (tid == 0) {
-                // room in the ring for this sub-tile's worst case
-                const uint32_t need_end = base + running / 32 + sub_words;
-                uint32_t spins = 0;
-                while (need_end - *ring_tail > RW) {
-                    if (++spins > kSpinLimit) { set_error(a.status, HUFF_ERR_TIMEOUT); break; }
-                    __nanosleep(32);
-                }
-                __threadfence_block();
-            }
-            if (!mbar_wait_bounded(&S.bars[s], parity)) set_error(a.status, HUFF_ERR_TIMEOUT);
-            const uint8_t *st = stage + s * kEncSubBytes;
-
-            // ---- reduce-merge: look up 2^r codewords and concatenate them in a register
-            uint64_t acc[kEncRPT][NR];
-            uint32_t rb[kEncRPT][NR];
-            uint32_t bits[kEncRPT];
-            uint32_t bad = 0;
-#pragma unroll
-            for (int k = 0; k < kEncRPT; k++) {
-                const uint32_t q = kEncRPT * tid + k;          // this thread's vectors are consecutive
-                uint32_t sv[V];
-                if (full) {
-                    const uint4 v = *reinterpret_cast<const uint4 *>(st + q * kEncVecBytes);
-                    sym_from_vec(v, sv, Sym());
-                    if (!GTAB && vec_out_of_table(v, tmask, Sym())) bad |= kBad32;
-                    bits[k] = merge_vec<Sym, Entry, GTAB, R2, true>(sv, V, tab, gcw, nbins, tmask, acc[k], rb[k], bad);
-                } else {
-                    const Sym *sp = reinterpret_cast<const Sym *>(a.sym);
-                    const uint64_t i0 = s0 + (uint64_t)q * V;
-                    const uint32_t vl = i0 >= a.n ? 0 : (a.n - i0 < V ? (uint32_t)(a.n - i0) : V);
-#pragma unroll
-                    for (int x = 0; x < V; x++) sv[x] = x < (int)vl ? (uint32_t)sp[i0 + x] : 0u;
-#pragma unroll
-                    for (int x = 0; x < V; x++)
-                        if (x < (int)vl && sv[x] > tmask) bad |= kBad32;
-                    bits[k] = merge_vec<Sym, Entry, GTAB, R2, false>(sv, vl, tab, gcw, nbins, tmask, acc[k], rb[k], bad);
-                }
-            }
-            if (bad & kBad32) {
-                // a symbol without codeword, or out of range: find out which
-                uint32_t code = HUFF_ERR_NOT_IN_CODEBOOK;
-#pragma unroll
-                for (int k = 0; k < kEncRPT; k++) {
-                    const uint32_t q = kEncRPT * tid + k;
-                    for (int x = 0; x < V; x++) {
-                        const uint64_t i = s0 + (uint64_t)q * V + x;
-                        if (i < a.n) {
-                            uint32_t sx = full ? (uint32_t)reinterpret_cast<const Sym *>(st + q * kEncVecBytes)[x]
-                                               : (uint32_t)reinterpret_cast<const Sym *>(a.sym)[i];
-                            if (sx >= nbins) code = HUFF_ERR_SYMBOL_RANGE;
-                        }
-                    }
-                }
-                set_error(a.status, code);
-            }
-
-            // ---- shuffle-merge as one scan: bit offset of this thread's runs in the tile
-            const uint32_t mine = bits[0] + bits[1];
-            uint32_t inc = mine;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
-                if (lane >= o) inc += y;
-            }
-            uint32_t *ws = S.wsum[it & 1];
-            if (lane == 31) ws[warp] = inc;
-            merge_sync();
-            // every merge thread has read stage s: refill it
-            if (tid == 0) produce_next<Sym>(a, prod, nsub, ntiles, stage, S.bars, stage_tile);
-            // exclusive prefix of the 8 warp totals, by shuffles
-            constexpr int NW = kEncThreads / 32;
-            const uint32_t wt = lane < NW ? ws[lane] : 0u;
-            uint32_t wi = wt;
-#pragma unroll
-            for (int o = 1; o < NW; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, wi, o);
-                if (lane >= o) wi += y;
-            }
-            const uint32_t wbase = __shfl_sync(0xFFFFFFFFu, wi - wt, warp);
-            const uint32_t Lsub = __shfl_sync(0xFFFFFFFFu, wi, NW - 1);
-            uint32_t pos = running + wbase + inc - mine;
-
-            // ---- place each merged run once; chunk offsets relative to the tile for now
-#pragma unroll
-            for (int k = 0; k < kEncRPT; k++) {
-                const uint32_t q = kEncRPT * tid + k;
-                if (small_chunks) {
-                    if ((q & (vpc - 1)) == 0 && (full || s0 + (uint64_t)q * V < a.n)) a.offs[(s0 + q * V) >> M] = pos;
-                } else if (q == 0 && (s0 & chunk_mask) == 0 && s0 < a.n) {
-                    a.offs[s0 >> M] = pos;
-                }
-#pragma unroll
-                for (int r = 0; r < NR; r++) {
-                    const uint32_t bb = rb[k][r];
-                    if (bb <= 64) {
-                        if (bb) place_run<RMASK>(ring, base, pos, acc[k][r], bb);
-                    } else {
-                        // longer than the register: write codeword by codeword
-                        BitSink<RMASK> sink;
-                        sink.begin(ring, base, pos);
-                        for (int x = 0; x < RL; x++) {
-                            const uint64_t i = s0 + (uint64_t)q * V + r * RL + x;
-                            if (i >= a.n) break;
-                            // the stage may be refilled already: read the symbol from global memory
-                            const uint32_t sx = (uint32_t)reinterpret_cast<const Sym *>(a.sym)[i];
-                            Entry en = table_get<Entry, GTAB>(tab, gcw, sx, nbins, tmask);
-                            const uint32_t l = ent_len<Entry>(en);
-                            if (l) sink.put64(ent_code<Entry>(en), l);
-                        }
-                        sink.end();
-                    }
-                    pos += bb;
-                }
-            }
-            running += Lsub;
-        }
-        merge_sync();                                      // tile bits complete in the ring
-        const uint32_t L = running;
-        if (tid == 0) {
-            // publish the tile's length and last 32 bits; hand it on
-            uint32_t last32 = 0;
-            if (L >= 32) {
-                uint32_t bb = L - 32, w = base + (bb >> 5), sh = bb & 31;
-                last32 = sh ? (ring[w & RMASK] << sh) | (ring[(w + 1) & RMASK] >> (32 - sh)) : ring[w & RMASK];
-            } else if (L) {
-                last32 = ring[base & RMASK] >> (32 - L);
-            }
-            st_relaxed_u64(&a.desc[2 * j], kFlagAgg | ((uint64_t)last32 << 24) | L);
-            if (j == 0) st_relaxed_u64(&a.desc[1], kFlagPre | L);
-            S.slot[sl].tile = j;
-            S.slot[sl].L = L;
-            S.slot[sl].base = base;
-            mbar_arrive(&S.full[sl]);
-        }
-        base += (L + 31) / 32;
-        merge_sync();                                      // stage_tile of the next tile written
-    }
-}
-
-// ---------------------------------------------------------------- look-back warp
-
-// Resolves the stream offset of each merged tile, in order.
-__device__ void lookback_loop(const EncArgs &a, uint64_t ntiles, EncShared &S) {
-    const uint32_t lane = threadIdx.x & 31;
-    for (uint32_t t = 0;; t++) {
-        const uint32_t sl = t % kSlots;
-        if (!mbar_wait_bounded(&S.full[sl], (t / kSlots) & 1)) {
-            if (lane == 0) set_error(a.status, HUFF_ERR_TIMEOUT);
-            return;
-        }
-        const uint64_t j = S.slot[sl].tile;
-        if (j < ntiles) {
-            const uint32_t L = S.slot[sl].L;
-            uint64_t G = 0;
-            uint32_t prev = 0;
-            if (j > 0) G = lookback_warp(a, j, L, &prev);
-            if (lane == 0) {
-                S.slot[sl].G = G;
-                S.slot[sl].prev = prev;
-                if (j == ntiles - 1) {
-                    a.offs[a.nchunks] = G + L;
-                    *a.total_bits = G + L;
-                }
-            }
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&S.gready[sl]);
-        if (j >= ntiles) return;
-    }
-}
-
-// ---------------------------------------------------------------- write-out warp
-
-// Copies each tile from the ring into the dense stream at its offset (the word
-// it shares with the previous tile is completed with the previous tile's last
-// bits), fixes the tile's chunk offsets and frees its ring words.
-template <typename Sym>
-__device__ void writeout_loop(const EncArgs &a, uint32_t *ring, uint64_t ntiles, uint32_t TILE, EncShared &S) {
-    constexpr uint32_t RMASK = ring_words<Sym>() - 1;
-    const uint32_t lane = threadIdx.x & 31;
-    const int M = a.chunk_log2;
-    const uint64_t chunk_mask = (1ull << M) - 1;
-    for (uint32_t t = 0;; t++) {
-        const uint32_t sl = t % kSlots;
-        if (!mbar_wait_bounded(&S.gready[sl], (t / kSlots) & 1)) {
-            if (lane == 0) set_error(a.status, HUFF_ERR_TIMEOUT);
-            return;
-        }
-        const uint64_t j = S.slot[sl].tile;
-        if (j >= ntiles) return;
-        const uint64_t G = S.slot[sl].G;
-        const uint32_t L = S.slot[sl].L, base = S.slot[sl].base, prev = S.slot[sl].prev;
-        const bool last = (j == ntiles - 1);
-        const uint32_t g = (uint32_t)(G & 31);
-        const uint64_t w0 = G >> 5;
-        const uint64_t end_bit = G + L;
-        const uint32_t nw = (uint32_t)((end_bit >> 5) - w0) + ((last && (end_bit & 31)) ? 1 : 0);
-        bool over = false;
-        // stream word w0 + i holds tile bits [32 i - g, 32 i - g + 32): four
-        // independent words per lane per step, each step four coalesced stores
-        const uint32_t sh = (32 - g) & 31;
-        for (uint32_t i0 = 0; i0 < nw; i0 += 128) {
-            uint32_t val[4];
-#pragma unroll
-            for (int k = 0; k < 4; k++) {
-                const uint32_t i = i0 + 32 * k + lane;
-                const uint32_t w = base + i - (g ? 1 : 0);      // ring word holding the word's first bit
-                const uint32_t hi = ring[w & RMASK], lo = ring[(w + 1) & RMASK];
-                val[k] = sh ? (hi << sh) | (lo >> (32 - sh)) : hi;
-                if (i == 0 && g) val[k] = ((prev & ((1u << g) - 1)) << (32 - g)) | (lo >> g);
-            }
-#pragma unroll
-            for (int k = 0; k < 4; k++) {
-                const uint32_t i = i0 + 32 * k + lane;
-                if (i < nw) {
-                    if (w0 + i < a.cap_words) a.out[w0 + i] = val[k]; else over = true;
-                }
-            }
-        }
-        if (over) set_error(a.status, HUFF_ERR_CAPACITY);
-        // chunk offsets were written relative to the tile
-        const uint64_t t0 = j * (uint64_t)TILE;
-        const uint64_t c_first = (t0 + chunk_mask) >> M;
-        const uint64_t tend = t0 + TILE < a.n ? t0 + TILE : a.n;
-        const uint64_t c_end = (tend + chunk_mask) >> M;
-        for (uint64_t c = c_first + lane; c < c_end; c += 32) a.offs[c] += G;
-        __syncwarp();
-        const uint32_t used = (L + 31) / 32;
-        for (uint32_t wz = 0; wz < used; wz += 128) {
-#pragma unroll
-            for (int k = 0; k < 4; k++) {
-                const uint32_t w = wz + 32 * k + lane;
-                if (w < used) ring[(base + w) & RMASK] = 0;
-            }
-        }
-        __syncwarp();
-        if (lane == 0) {
-            __threadfence_block();
-            *(volatile uint32_t *)&S.ring_tail = base + used;
-            mbar_arrive(&S.sfree[sl]);
-        }
-        __syncwarp();
-    }
-}
-
-// ---------------------------------------------------------------- kernel
-
-// Reduction factor for this launch: the caller's, or the rule of Sec. IV-C,
-// floor(log2 beta) + r + 1 = log2(32) with beta the average codeword length;
-// capped so a run stays inside one 16-byte vector.
-template <typename Sym>
-__device__ __forceinline__ int pick_r(const EncArgs &a, const huff_codebook_header *hdr) {
-    constexpr int RMAX = sizeof(Sym) == 1 ? 4 : sizeof(Sym) == 2 ? 3 : 2;
-    constexpr int RMIN = sizeof(Sym) == 4 ? 0 : 2;     // at most 4 registers per thread hold runs
-    int r = a.reduce_log2;
-    if (r < 0) {
-        const uint64_t tb = hdr->total_bits, ns = hdr->nsymbols;
-        // floor(log2(beta)): largest f with ns * 2^f <= tb
-        int f = 0;
-        while (f < 62 && ns && (ns << (f + 1)) <= tb && (ns << (f + 1)) >> (f + 1) == ns) f++;
-        r = 4 - f;
-    }
-    return r < RMIN ? RMIN : (r > RMAX ? RMAX : r);
-}
-
-template <typename Sym, typename Entry, bool GTAB>
-__device__ void merge_dispatch(int r, const EncArgs &a, uint8_t *stage, uint32_t *ring, const Entry *tab,
-                               uint32_t nbins, uint32_t tmask, uint32_t nsub, uint32_t max_len, EncShared &S) {
-    switch (r) {
-        case 0: if constexpr (VecOf<Sym>::N <= 4) merge_warps<Sym, Entry, GTAB, 0>(a, stage, ring, tab, nbins, tmask, nsub, max_len, S); break;
-        case 1: if constexpr (VecOf<Sym>::N <= 4) merge_warps<Sym, Entry, GTAB, 1>(a, stage, ring, tab, nbins, tmask, nsub, max_len, S); break;
-        case 2: merge_warps<Sym, Entry, GTAB, 2>(a, stage, ring, tab, nbins, tmask, nsub, max_len, S); break;
-        case 3: if constexpr (VecOf<Sym>::N >= 8) merge_warps<Sym, Entry, GTAB, 3>(a, stage, ring, tab, nbins, tmask, nsub, max_len, S); break;
-        default: if constexpr (VecOf<Sym>::N >= 16) merge_warps<Sym, Entry, GTAB, 4>(a, stage, ring, tab, nbins, tmask, nsub, max_len, S); break;
-    }
-}
-
-template <typename Sym, bool GTAB>
-__global__ void __launch_bounds__(kEncCtaThreads, sizeof(Sym) == 1 ? 2 : 3) encode_kernel(EncArgs a) {
-    extern __shared__ __align__(128) uint8_t smem[];
-    constexpr uint32_t RW = ring_words<Sym>();
-    uint8_t *stage = smem;
-    uint32_t *ring = reinterpret_cast<uint32_t *>(smem + kEncStages * kEncSubBytes);
-    uint64_t *tab = reinterpret_cast<uint64_t *>(ring + RW);
-    __shared__ EncShared S;
-
-    const huff_codebook_header *hdr = reinterpret_cast<const huff_codebook_header *>(a.book);
-    const uint32_t nbins = hdr->nbins;
-    const uint32_t max_len = hdr->max_len;
-    const uint64_t *gcw = reinterpret_cast<const uint64_t *>(a.book + cb_cw_offset());
-    const bool small = max_len <= 23;
-    const uint32_t nsub = enc_subs_per_tile<Sym>(max_len);
-    if (max_len > kEncMaxLen || nbins != a.nbins) {
-        if (threadIdx.x == 0) set_error(a.status, HUFF_ERR_INVALID_ARG);
-        return;
-    }
-    for (uint32_t i = threadIdx.x; i < RW; i += blockDim.x) ring[i] = 0;
-    uint32_t tslots = 1;
-    while (tslots < nbins) tslots <<= 1;
-    const uint32_t tmask = tslots - 1;
-    if (!GTAB) {
-        if (small) {
-            uint32_t *t32 = reinterpret_cast<uint32_t *>(tab);
-            for (uint32_t i = threadIdx.x; i < tslots; i += blockDim.x)
-                t32[i] = entry_from_cw<uint32_t>(i < nbins ? gcw[i] : 0ull);
-        } else {
-            for (uint32_t i = threadIdx.x; i < tslots; i += blockDim.x) tab[i] = i < nbins ? gcw[i] : 0ull;
-        }
-    }
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < kEncStages; s++) mbar_init(&S.bars[s], 1);
-        for (int b = 0; b < kSlots; b++) {
-            mbar_init(&S.full[b], 1);
-            mbar_init(&S.gready[b], 1);
-            mbar_init(&S.sfree[b], 1);
-        }
-        S.ring_tail = 0;
-        fence_barrier_init();
-    }
-    __syncthreads();
-    const uint32_t TILE = enc_sub_syms<Sym>() * nsub;
-    const uint64_t ntiles = (a.n + TILE - 1) / TILE;
-    if (threadIdx.x >= kEncThreads + 32) {
-        writeout_loop<Sym>(a, ring, ntiles, TILE, S);
-        return;
-    }
-    if (threadIdx.x >= kEncThreads) {
-        lookback_loop(a, ntiles, S);
-        return;
-    }
-    const int r = pick_r<Sym>(a, hdr);
-    if (small)
-        merge_dispatch<Sym, uint32_t, GTAB>(r, a, stage, ring, reinterpret_cast<const uint32_t *>(tab), nbins, tmask,
-                                            nsub, max_len, S);
-    else
-        merge_dispatch<Sym, uint64_t, GTAB>(r, a, stage, ring, tab, nbins, tmask, nsub, max_len, S);
-}
-
-// ---------------------------------------------------------------- host side
 
 size_t encode_scratch_bytes(uint64_t n) {
     // counter + one 16-byte descriptor per tile (at most one tile per u32 sub-tile)
@@ -808,11 +11,10 @@ size_t encode_scratch_bytes(uint64_t n) {
     return 64 + 16 * ntiles;
 }
 
-template <typename Sym>
-static size_t enc_smem_bytes(bool gtab, uint32_t nbins) {
-    uint32_t tslots = 1;
-    while (tslots < nbins) tslots <<= 1;
-    return kEncStages * kEncSubBytes + ring_words<Sym>() * 4 + (gtab ? 0 : tslots * 8ull);
+static uint32_t pow2_at_least(uint32_t x) {
+    uint32_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
 }
 
 template <typename Sym>
@@ -820,34 +22,39 @@ static huff_status launch_encode(const void *d_sym, uint64_t n, const void *d_co
                                  int chunk_log2, int reduce_log2, uint32_t *d_out, uint64_t cap, uint64_t *d_offs,
                                  uint64_t *d_total, uint8_t *scratch, uint32_t *status, cudaStream_t st) {
     constexpr uint32_t SUB = enc_sub_syms<Sym>();
-    EncArgs a;
-    a.sym = static_cast<const uint8_t *>(d_sym);
-    a.n = n;
-    a.max_tiles = (n + SUB - 1) / SUB;
-    a.nchunks = (n + (1ull << chunk_log2) - 1) >> chunk_log2;
-    a.book = static_cast<const uint8_t *>(d_codebook);
-    a.out = d_out;
-    a.cap_words = cap;
-    a.offs = d_offs;
-    a.total_bits = d_total;
+    EncArgs a{};
+    a.one.sym = static_cast<const uint8_t *>(d_sym);
+    a.one.book = static_cast<const uint8_t *>(d_codebook);
+    a.one.out = d_out;
+    a.one.offs = d_offs;
+    a.one.total_bits = d_total;
+    a.one.status = status;
+    a.one.n = n;
+    a.one.cap_words = cap;
+    a.one.nchunks = (n + (1ull << chunk_log2) - 1) >> chunk_log2;
+    a.one.nbins = nbins_host;
+    a.one.chunk_log2 = chunk_log2;
+    a.one.aligned = ((uintptr_t)d_sym & 15) == 0;
+    a.fields = nullptr;
+    a.conf = nullptr;
+    a.nfields = 1;
+    a.tslots = pow2_at_least(nbins_host);
     a.tile_counter = reinterpret_cast<uint32_t *>(scratch);
     a.desc = reinterpret_cast<uint64_t *>(scratch + 64);
-    a.status = status;
-    a.chunk_log2 = chunk_log2;
     a.reduce_log2 = reduce_log2;
-    a.aligned = ((uintptr_t)d_sym & 15) == 0;
-    a.nbins = nbins_host;
-    if (cudaMemsetAsync(scratch, 0, 64 + 16 * a.max_tiles, st) != cudaSuccess) return HUFF_ERR_CUDA;
+    a.nsub_cap = kEncMaxSubs;
+    const uint64_t max_tiles = (n + SUB - 1) / SUB;
+    if (cudaMemsetAsync(scratch, 0, 64 + 16 * max_tiles, st) != cudaSuccess) return HUFF_ERR_CUDA;
     const bool gtab = nbins_host > kEncSmemTableBins;
-    size_t smem = enc_smem_bytes<Sym>(gtab, nbins_host);
-    void (*kern)(EncArgs) = gtab ? encode_kernel<Sym, true> : encode_kernel<Sym, false>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    const size_t smem = enc_smem_bytes<Sym>(gtab, a.tslots, 0);
+    void (*kern)(EncArgs) = gtab ? encode_kernel<Sym, true, false> : encode_kernel<Sym, false, false>;
+    if (!allow_dynamic_smem((const void *)kern, smem))
         return HUFF_ERR_CUDA;
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kEncCtaThreads, smem);
     if (occ < 1) occ = 1;
     uint64_t grid = (uint64_t)sm_count() * occ;
-    if (grid > a.max_tiles) grid = a.max_tiles;
+    if (grid > max_tiles) grid = max_tiles;
     kern<<<(unsigned)grid, kEncCtaThreads, smem, st>>>(a);
     note_launch();
     return cudaGetLastError() == cudaSuccess ? HUFF_OK : HUFF_ERR_CUDA;
@@ -862,6 +69,19 @@ huff_status encode_launch(const void *d_sym, uint64_t n, huff_dtype dtype, const
         case HUFF_U32: return launch_encode<uint32_t>(d_sym, n, d_codebook, nbins, chunk_log2, reduce_log2, d_out, cap, d_offs, d_total, scratch, status, st);
     }
     return HUFF_ERR_INVALID_ARG;
+}
+
+uint32_t encode_sub_symbols(huff_dtype dtype) {
+    return dtype == HUFF_U8 ? enc_sub_syms<uint8_t>() : dtype == HUFF_U16 ? enc_sub_syms<uint16_t>()
+                                                                          : enc_sub_syms<uint32_t>();
+}
+
+void encode_r_range(huff_dtype dtype, int *r_min, int *r_max) {
+    switch (dtype) {
+        case HUFF_U8: *r_min = enc_r_min<uint8_t>(); *r_max = enc_r_max<uint8_t>(); return;
+        case HUFF_U16: *r_min = enc_r_min<uint16_t>(); *r_max = enc_r_max<uint16_t>(); return;
+        default: *r_min = enc_r_min<uint32_t>(); *r_max = enc_r_max<uint32_t>(); return;
+    }
 }
 
 int encode_run_log2(huff_dtype dtype) {

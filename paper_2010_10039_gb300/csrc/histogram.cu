@@ -11,7 +11,7 @@
 // histogram.  Alphabets too large for 32-bit counters in shared memory use
 // packed 16-bit counters (bins k and k + 32768 share a word) that are flushed
 // to the global histogram before any of them can wrap.
-#include "common.cuh"
+#include "kernels.cuh"
 
 namespace huff {
 
@@ -77,26 +77,27 @@ __device__ __forceinline__ void count_vec(uint32_t *h, const uint4 &v, uint32_t 
 // Folds the shared-memory counts into the global histogram; counts in slots
 // at or past nbins are symbols out of range: they set *bad and are dropped.
 template <bool PACKED>
-__device__ void hist_flush(uint32_t *hsm, const HistArgs &a, uint32_t &bad) {
+__device__ void hist_flush(uint32_t *hsm, uint32_t *hist, uint32_t nbins, uint32_t mask, uint32_t nrep,
+                           uint32_t stride, uint32_t &bad) {
     if (PACKED) {
         for (uint32_t w = threadIdx.x; w < kPackedWords; w += blockDim.x) {
             uint32_t v = hsm[w];
             if (v) {
                 if (v & 0xFFFFu) {
-                    if (w < a.nbins) atomicAdd(a.hist + w, v & 0xFFFFu); else bad = 1;
+                    if (w < nbins) atomicAdd(hist + w, v & 0xFFFFu); else bad = 1;
                 }
                 if (v >> 16) {
-                    if (w + kPackedWords < a.nbins) atomicAdd(a.hist + w + kPackedWords, v >> 16); else bad = 1;
+                    if (w + kPackedWords < nbins) atomicAdd(hist + w + kPackedWords, v >> 16); else bad = 1;
                 }
                 hsm[w] = 0;
             }
         }
     } else {
-        for (uint32_t k = threadIdx.x; k <= a.mask; k += blockDim.x) {
+        for (uint32_t k = threadIdx.x; k <= mask; k += blockDim.x) {
             uint32_t sum = 0;
-            for (uint32_t r = 0; r < a.nrep; r++) sum += hsm[r * a.stride + k];
+            for (uint32_t r = 0; r < nrep; r++) sum += hsm[r * stride + k];
             if (sum) {
-                if (k < a.nbins) atomicAdd(a.hist + k, sum); else bad = 1;
+                if (k < nbins) atomicAdd(hist + k, sum); else bad = 1;
             }
         }
     }
@@ -130,14 +131,14 @@ __global__ void __launch_bounds__(kHistThreads, 2) hist_kernel(HistArgs a) {
         }
         if (PACKED && ++since == kRoundsPerEpoch) {
             __syncthreads();
-            hist_flush<true>(hsm, a, bad);
+            hist_flush<true>(hsm, a.hist, a.nbins, a.mask, a.nrep, a.stride, bad);
             __syncthreads();
             since = 0;
         }
     }
     if (PACKED) {
         __syncthreads();
-        hist_flush<true>(hsm, a, bad);
+        hist_flush<true>(hsm, a.hist, a.nbins, a.mask, a.nrep, a.stride, bad);
         __syncthreads();
     }
     // head (before the first aligned address) and tail (after the last whole vector)
@@ -149,8 +150,58 @@ __global__ void __launch_bounds__(kHistThreads, 2) hist_kernel(HistArgs a) {
         count_one<PACKED>(my, sp[idx], mask, seen);
     }
     __syncthreads();
-    hist_flush<PACKED>(hsm, a, bad);
+    hist_flush<PACKED>(hsm, a.hist, a.nbins, a.mask, a.nrep, a.stride, bad);
     if (bad || seen > mask) set_error(a.status, HUFF_ERR_SYMBOL_RANGE);
+}
+
+// ---------------------------------------------------------------- batched histogram
+
+// Every CTA counts whole tiles (CTA-strided over the tile list) into its
+// replicas and folds them into the tile's field after each tile.  Tiles of a
+// packed (> 16384-bin) batch hold at most 65,535 symbols, so 16-bit counters
+// never wrap.
+template <typename Sym, bool PACKED>
+__global__ void __launch_bounds__(kHistThreads, 2) hist_batch_kernel(const HistTile *tiles, uint32_t ntiles,
+                                                                      const HistField *fields, uint32_t mask,
+                                                                      uint32_t nrep, uint32_t stride) {
+    extern __shared__ __align__(16) uint32_t hsm[];
+    constexpr int V = SymVec<Sym>::N;
+    const uint32_t words = PACKED ? kPackedWords : nrep * stride;
+    uint32_t *my = PACKED ? hsm : hsm + ((threadIdx.x >> 5) % nrep) * stride;
+    for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) hsm[i] = 0;
+    for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        __syncthreads();
+        const HistTile T = tiles[t];
+        const HistField F = fields[T.field];
+        const Sym *sp = reinterpret_cast<const Sym *>(F.sym);
+        uint32_t seen = 0, bad = 0;
+        // [start, a0) scalars, whole vectors from a0, then a scalar tail
+        const uint64_t a0 = T.start + F.head < T.end ? T.start + F.head : T.end;
+        const uint64_t nv = (T.end - a0) / V;
+        const uint64_t tail0 = a0 + nv * V;
+        if (threadIdx.x < a0 - T.start) count_one<PACKED>(my, sp[T.start + threadIdx.x], mask, seen);
+        if (threadIdx.x < T.end - tail0) count_one<PACKED>(my, sp[tail0 + threadIdx.x], mask, seen);
+        const uint4 *vec = reinterpret_cast<const uint4 *>(sp + a0);
+        uint64_t i = threadIdx.x;
+        for (; i + 3 * kHistThreads < nv; i += 4 * kHistThreads) {
+            const uint4 v0 = vec[i], v1 = vec[i + kHistThreads], v2 = vec[i + 2 * kHistThreads],
+                        v3 = vec[i + 3 * kHistThreads];
+            count_vec<Sym, PACKED>(my, v0, mask, seen);
+            count_vec<Sym, PACKED>(my, v1, mask, seen);
+            count_vec<Sym, PACKED>(my, v2, mask, seen);
+            count_vec<Sym, PACKED>(my, v3, mask, seen);
+        }
+        for (; i < nv; i += kHistThreads) count_vec<Sym, PACKED>(my, vec[i], mask, seen);
+        __syncthreads();
+        if (PACKED) {
+            hist_flush<true>(hsm, F.hist, F.nbins, mask, 1, kPackedWords, bad);    // also clears the counters
+        } else {
+            hist_flush<false>(hsm, F.hist, F.nbins, mask, nrep, stride, bad);
+            __syncthreads();
+            for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) hsm[w] = 0;
+        }
+        if (bad || seen > mask) set_error(F.status, HUFF_ERR_SYMBOL_RANGE);
+    }
 }
 
 template <typename Sym>
@@ -184,7 +235,7 @@ static huff_status launch_hist(const void *d_sym, uint64_t n, uint32_t nbins, ui
         smem = (size_t)a.nrep * a.stride * 4;
     }
     void (*kern)(HistArgs) = packed ? hist_kernel<Sym, true> : hist_kernel<Sym, false>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    if (!allow_dynamic_smem((const void *)kern, smem))
         return HUFF_ERR_CUDA;
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kHistThreads, smem);
@@ -197,6 +248,78 @@ static huff_status launch_hist(const void *d_sym, uint64_t n, uint32_t nbins, ui
     kern<<<(unsigned)grid, kHistThreads, smem, st>>>(a);
     note_launch();
     return cudaGetLastError() == cudaSuccess ? HUFF_OK : HUFF_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------- batched launch
+
+uint64_t histogram_batch_tile(uint32_t max_nbins) { return max_nbins > 16384 ? 32768 : 131072; }
+
+// Replica layout of a batched launch whose largest alphabet is max_nbins.
+static void batch_layout(uint32_t max_nbins, uint32_t *mask, uint32_t *nrep, uint32_t *stride, size_t *smem) {
+    uint32_t slots = 1;
+    while (slots < max_nbins) slots <<= 1;
+    *mask = slots - 1;
+    if (max_nbins > 16384) {
+        *nrep = 1;
+        *stride = kPackedWords;
+        *smem = kPackedWords * 4;
+    } else {
+        *stride = slots + 1;
+        const uint32_t warps = kHistThreads / 32;
+        uint32_t r = (uint32_t)((100 * 1024) / (*stride * 4ull));
+        *nrep = r > warps ? warps : (r < 1 ? 1 : r);
+        *smem = (size_t)*nrep * *stride * 4;
+    }
+}
+
+template <typename Sym>
+static void (*batch_kernel(uint32_t max_nbins))(const HistTile *, uint32_t, const HistField *, uint32_t, uint32_t,
+                                                 uint32_t) {
+    return max_nbins > 16384 ? hist_batch_kernel<Sym, true> : hist_batch_kernel<Sym, false>;
+}
+
+template <typename Sym>
+static huff_status batch_prepare(uint32_t max_nbins, int *ctas_per_sm) {
+    uint32_t mask, nrep, stride;
+    size_t smem;
+    batch_layout(max_nbins, &mask, &nrep, &stride, &smem);
+    auto kern = batch_kernel<Sym>(max_nbins);
+    if (!allow_dynamic_smem((const void *)kern, smem))
+        return HUFF_ERR_CUDA;
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kHistThreads, smem);
+    *ctas_per_sm = occ < 1 ? 1 : occ;
+    return HUFF_OK;
+}
+
+template <typename Sym>
+static huff_status batch_launch(const HistTile *d_tiles, uint32_t ntiles, const HistField *d_fields,
+                                uint32_t max_nbins, uint32_t grid, cudaStream_t st) {
+    uint32_t mask, nrep, stride;
+    size_t smem;
+    batch_layout(max_nbins, &mask, &nrep, &stride, &smem);
+    batch_kernel<Sym>(max_nbins)<<<grid, kHistThreads, smem, st>>>(d_tiles, ntiles, d_fields, mask, nrep, stride);
+    note_launch();
+    return cudaGetLastError() == cudaSuccess ? HUFF_OK : HUFF_ERR_CUDA;
+}
+
+huff_status histogram_batch_prepare(huff_dtype dtype, uint32_t max_nbins, int *ctas_per_sm) {
+    switch (dtype) {
+        case HUFF_U8: return batch_prepare<uint8_t>(max_nbins, ctas_per_sm);
+        case HUFF_U16: return batch_prepare<uint16_t>(max_nbins, ctas_per_sm);
+        case HUFF_U32: return batch_prepare<uint32_t>(max_nbins, ctas_per_sm);
+    }
+    return HUFF_ERR_INVALID_ARG;
+}
+
+huff_status histogram_batch_launch(huff_dtype dtype, const HistTile *d_tiles, uint32_t ntiles,
+                                   const HistField *d_fields, uint32_t max_nbins, uint32_t grid, cudaStream_t st) {
+    switch (dtype) {
+        case HUFF_U8: return batch_launch<uint8_t>(d_tiles, ntiles, d_fields, max_nbins, grid, st);
+        case HUFF_U16: return batch_launch<uint16_t>(d_tiles, ntiles, d_fields, max_nbins, grid, st);
+        case HUFF_U32: return batch_launch<uint32_t>(d_tiles, ntiles, d_fields, max_nbins, grid, st);
+    }
+    return HUFF_ERR_INVALID_ARG;
 }
 
 huff_status histogram_launch(const void *d_sym, uint64_t n, huff_dtype dtype, uint32_t nbins,

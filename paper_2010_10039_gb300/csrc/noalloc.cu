@@ -7,14 +7,9 @@
 // caller workspace.
 #include <mutex>
 
-#include "common.cuh"
+#include "kernels.cuh"
 
 namespace huff {
-
-huff_status encode_launch(const void *, uint64_t, huff_dtype, const void *, uint32_t, int, int, uint32_t *, uint64_t,
-                          uint64_t *, uint64_t *, uint8_t *, uint32_t *, cudaStream_t);
-size_t encode_scratch_bytes(uint64_t n);
-int encode_run_log2(huff_dtype dtype);
 
 // Largest input of one call, and the encoder scratch it needs (2 MiB + 64
 // bytes: a tile counter and a 16-byte descriptor per tile of >= 2048 symbols).
@@ -64,6 +59,9 @@ extern "C" huff_status huff_encode_noalloc(const void *d_sym, uint64_t n, huff_d
     if (dtype != HUFF_U8 && dtype != HUFF_U16 && dtype != HUFF_U32) return HUFF_ERR_INVALID_ARG;
     if (nbins < 1 || nbins > HUFF_MAX_BINS || (dtype == HUFF_U8 && nbins > 256)) return HUFF_ERR_INVALID_ARG;
     if (((uintptr_t)d_codebook & 15) != 0) return HUFF_ERR_INVALID_ARG;
+    if (((uintptr_t)d_sym % (uintptr_t)dtype) != 0 || ((uintptr_t)d_out & 3) != 0 ||
+        ((uintptr_t)d_chunk_bit_offset & 7) != 0 || ((uintptr_t)d_total_bits & 7) != 0 || ((uintptr_t)d_status & 3) != 0)
+        return HUFF_ERR_INVALID_ARG;
     if (prm.chunk_log2 < 4 || prm.chunk_log2 > 30 || prm.chunk_log2 < encode_run_log2(dtype)) return HUFF_ERR_INVALID_ARG;
     if (prm.reduce_log2 != -1 && (prm.reduce_log2 < 0 || prm.reduce_log2 > prm.chunk_log2)) return HUFF_ERR_INVALID_ARG;
     huff_status err = HUFF_OK;

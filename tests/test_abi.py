@@ -68,3 +68,43 @@ def test_default_params(lib):
     import paper_2010_10039_gb300 as huff
     p = huff.huff_default_params()
     assert (p.chunk_log2, p.reduce_log2, p.block_threads, p.merge) == (10, -1, 0, 0)
+
+
+def test_misaligned_typed_pointers_are_rejected_on_the_host(lib):
+    """A u16/u32 symbol pointer that is not element aligned returns
+    HUFF_ERR_INVALID_ARG before any device work (no GPU needed)."""
+    import paper_2010_10039_gb300 as huff
+    L = huff.lib()
+    bad16 = 0x100001          # odd: never dereferenced
+    assert L.huff_histogram(bad16, 100, huff.HUFF_U16, 1024, 0x200000, 0x300000, None) == 1
+    assert L.huff_histogram(0x100002, 100, huff.HUFF_U32, 1024, 0x200000, 0x300000, None) == 1
+    p = huff.huff_default_params()
+    assert L.huff_encode(bad16, 100, huff.HUFF_U16, 0x400000, 1024, ctypes.byref(p), 0x500000, 100,
+                         0x600000, 0x700000, 0x300000, None) == 1
+
+
+def test_batch_plan_create_rejects_bad_fields_on_the_host(lib):
+    import paper_2010_10039_gb300 as huff
+    L = huff.lib()
+    out = ctypes.c_void_p()
+    cfg = huff.huff_batch_cfg()
+    L.huff_batch_default_cfg(ctypes.byref(cfg))
+    assert (cfg.autotune, cfg.reduce_log2, cfg.max_subtiles, cfg.ctas_per_sm) == (0, -1, 0, 0)
+    arr = (huff.huff_field * 1)()
+    good = dict(d_sym=0x100000, n=1000, dtype=huff.HUFF_U16, nbins=1024, chunk_log2=10, d_out=0x200000,
+                out_capacity_words=1000, d_chunk_bit_offset=0x300000, d_total_bits=0x400000)
+    cases = [dict(nbins=0), dict(nbins=70000), dict(dtype=3), dict(dtype=huff.HUFF_U8, nbins=300),
+             dict(d_sym=0x100001), dict(d_total_bits=0x400004), dict(chunk_log2=2), dict(chunk_log2=31),
+             dict(n=1 << 32), dict(d_out=0)]
+    for c in cases:
+        f = dict(good)
+        f.update(c)
+        for k, v in f.items():
+            setattr(arr[0], k, v)
+        assert L.huff_batch_plan_create(arr, 1, ctypes.byref(cfg), None, ctypes.byref(out)) == 1, c
+        assert not out.value
+    assert L.huff_batch_plan_create(arr, 0, ctypes.byref(cfg), None, ctypes.byref(out)) == 1
+    bad_cfg = huff.huff_batch_cfg(0, 7, 0, 0)
+    for k, v in good.items():
+        setattr(arr[0], k, v)
+    assert L.huff_batch_plan_create(arr, 1, ctypes.byref(bad_cfg), None, ctypes.byref(out)) == 1
