@@ -371,6 +371,39 @@ __device__ __forceinline__ void produce_next(const EncArgs &a, const EncField *f
     p.slot++;
 }
 
+// Producer of a single-field launch: the field is the kernel parameter, so
+// only the position lives in (thread 0's) registers.
+struct ProducerOne {
+    uint32_t tile;
+    uint32_t next;
+    uint32_t sub;
+    uint32_t slot;
+};
+
+template <typename Sym>
+__device__ __forceinline__ void produce_next_one(const EncArgs &a, ProducerOne &p, uint32_t nsub, uint32_t total,
+                                                 uint8_t *stage, uint64_t *bars, volatile uint32_t *s_stage_tile) {
+    constexpr uint32_t SUB = enc_sub_syms<Sym>();
+    if (p.sub >= nsub && p.tile < total) {
+        p.tile = p.next;
+        p.next = p.tile < total ? atomicAdd(a.tile_counter, 1u) : p.tile;
+        p.sub = 0;
+    }
+    const int s = (int)(p.slot % kEncStages);
+    s_stage_tile[s] = p.tile;
+    if (p.tile < total) {
+        const uint64_t s0 = ((uint64_t)p.tile * nsub + p.sub) * SUB;
+        if (a.one.aligned && s0 + SUB <= a.one.n) {
+            mbar_arrive_expect_tx(&bars[s], kEncSubBytes);
+            bulk_g2s(stage + s * kEncSubBytes, a.one.sym + s0 * sizeof(Sym), kEncSubBytes, &bars[s]);
+        } else {
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bars[s])) : "memory");
+        }
+    }
+    p.sub++;
+    p.slot++;
+}
+
 __device__ __forceinline__ void merge_sync() {       // the 8 merge warps only
     asm volatile("bar.sync 1, %0;" ::"n"(kEncThreads) : "memory");
 }
@@ -456,7 +489,8 @@ __device__ __forceinline__ void load_table(Entry *tab, uint32_t tslots, const En
 // 2^r codewords per register.
 template <typename Sym, typename Entry, bool GTAB, int R2, bool BATCH>
 __device__ void merge_warps(const EncArgs &a, const EncField *fields, const uint32_t *tbase, uint8_t *stage,
-                            uint32_t *ring, Entry *tab, uint32_t total, EncShared &S) {
+                            uint32_t *ring, Entry *tab, uint32_t total, uint32_t nsub1, uint32_t max_len1,
+                            EncShared &S) {
     constexpr int V = VecOf<Sym>::N;              // symbols per 16-byte vector
     constexpr int RL = 1 << R2;                   // symbols per merged run
     constexpr int NR = V / RL;                    // runs per vector
@@ -470,19 +504,27 @@ __device__ void merge_warps(const EncArgs &a, const EncField *fields, const uint
     volatile uint32_t *stage_field = S.stage_field;
     volatile uint32_t *ring_tail = &S.ring_tail;
 
-    // the producer's state lives in shared memory: only thread 0 touches it,
-    // and it would otherwise hold registers in every merge thread
+    // A batch producer keeps its state in shared memory (only thread 0 touches
+    // it, and it would otherwise hold registers in every merge thread); a
+    // single-field producer needs four registers.
     Producer &prod = S.prod;
+    ProducerOne one{0u, 0u, nsub1, 0u};
     if (tid == 0) {
-        prod.slot = 0;
-        prod.sub = 0;
-        prod.nsub = 0;
-        prod.tile = 0;
-        prod.next = 0;
-        prod.f = 0;
-        prod.next = atomicAdd(a.tile_counter, 1u);
-        for (int i = 0; i < kEncStages; i++)
-            produce_next<Sym, BATCH>(a, fields, tbase, prod, total, stage, S.bars, stage_tile, stage_field);
+        if (BATCH) {
+            prod.slot = 0;
+            prod.sub = 0;
+            prod.nsub = 0;
+            prod.tile = 0;
+            prod.f = 0;
+            prod.next = atomicAdd(a.tile_counter, 1u);
+        } else {
+            one.next = atomicAdd(a.tile_counter, 1u);
+            stage_field[0] = stage_field[1] = stage_field[2] = stage_field[3] = 0;
+        }
+        for (int i = 0; i < kEncStages; i++) {
+            if (BATCH) produce_next<Sym, true>(a, fields, tbase, prod, total, stage, S.bars, stage_tile, stage_field);
+            else produce_next_one<Sym>(a, one, nsub1, total, stage, S.bars, stage_tile);
+        }
     }
     merge_sync();
 
@@ -502,19 +544,21 @@ __device__ void merge_warps(const EncArgs &a, const EncField *fields, const uint
         }
         if (f != cur_f) {
             // every merge thread is past its last lookup in the previous field's table
-            if (!GTAB) load_table<Entry>(tab, a.tslots, fields[f]);
-            if (tid == 0) S.mf = fields[f];
+            if (!GTAB) load_table<Entry>(tab, a.tslots, BATCH ? fields[f] : a.one);
+            if (BATCH && tid == 0) S.mf = fields[f];
             cur_f = f;
             merge_sync();
         }
-        // the field's values are read from shared memory where they are used,
-        // so they hold no registers across the merge loop
-        const EncField &F = S.mf;
-        const uint64_t j = g - F.tile_base;
-        const uint64_t t0 = j * (uint64_t)(SUB * F.nsub);
+        // A batch reads the field's values from shared memory where they are
+        // used, so they hold no registers across the merge loop; a single-field
+        // launch reads them from the kernel parameters.
+        const EncField &F = BATCH ? S.mf : a.one;
+        const uint32_t nsub = BATCH ? S.mf.nsub : nsub1;
+        const uint64_t j = BATCH ? g - S.mf.tile_base : g;
+        const uint64_t t0 = j * (uint64_t)(SUB * nsub);
         uint32_t running = 0;
 
-        for (uint32_t sub = 0; sub < F.nsub; sub++, it++) {
+        for (uint32_t sub = 0; sub < nsub; sub++, it++) {
             const uint64_t n = F.n;
             const uint32_t nbins = F.nbins;
             const Sym *symp = reinterpret_cast<const Sym *>(F.sym);
@@ -526,7 +570,7 @@ __device__ void merge_warps(const EncArgs &a, const EncField *fields, const uint
             const bool full = F.aligned && s0 + SUB <= n;
             if (tid == 0) {
                 // room in the ring for this sub-tile's worst case
-                const uint32_t sub_words = (SUB * F.max_len + 31) / 32 + 2;
+                const uint32_t sub_words = (SUB * (BATCH ? S.mf.max_len : max_len1) + 31) / 32 + 2;
                 const uint32_t need_end = base + running / 32 + sub_words;
                 uint32_t spins = 0;
                 while (need_end - *ring_tail > RW) {
@@ -593,8 +637,10 @@ __device__ void merge_warps(const EncArgs &a, const EncField *fields, const uint
             if (lane == 31) ws[warp] = inc;
             merge_sync();
             // every merge thread has read stage s: refill it
-            if (tid == 0)
-                produce_next<Sym, BATCH>(a, fields, tbase, prod, total, stage, S.bars, stage_tile, stage_field);
+            if (tid == 0) {
+                if (BATCH) produce_next<Sym, true>(a, fields, tbase, prod, total, stage, S.bars, stage_tile, stage_field);
+                else produce_next_one<Sym>(a, one, nsub1, total, stage, S.bars, stage_tile);
+            }
             // exclusive prefix of the 8 warp totals, by shuffles
             constexpr int NW = kEncThreads / 32;
             const uint32_t wt = lane < NW ? ws[lane] : 0u;
@@ -819,13 +865,14 @@ __host__ __device__ inline int enc_rule_r(uint64_t total_bits, uint64_t nsymbols
 
 template <typename Sym, typename Entry, bool GTAB, bool BATCH>
 __device__ void merge_dispatch(int r, const EncArgs &a, const EncField *fields, const uint32_t *tbase,
-                               uint8_t *stage, uint32_t *ring, Entry *tab, uint32_t total, EncShared &S) {
+                               uint8_t *stage, uint32_t *ring, Entry *tab, uint32_t total, uint32_t nsub1,
+                               uint32_t max_len1, EncShared &S) {
     switch (r) {
-        case 0: if constexpr (VecOf<Sym>::N <= 4) merge_warps<Sym, Entry, GTAB, 0, BATCH>(a, fields, tbase, stage, ring, tab, total, S); break;
-        case 1: if constexpr (VecOf<Sym>::N <= 4) merge_warps<Sym, Entry, GTAB, 1, BATCH>(a, fields, tbase, stage, ring, tab, total, S); break;
-        case 2: merge_warps<Sym, Entry, GTAB, 2, BATCH>(a, fields, tbase, stage, ring, tab, total, S); break;
-        case 3: if constexpr (VecOf<Sym>::N >= 8) merge_warps<Sym, Entry, GTAB, 3, BATCH>(a, fields, tbase, stage, ring, tab, total, S); break;
-        default: if constexpr (VecOf<Sym>::N >= 16) merge_warps<Sym, Entry, GTAB, 4, BATCH>(a, fields, tbase, stage, ring, tab, total, S); break;
+        case 0: if constexpr (VecOf<Sym>::N <= 4) merge_warps<Sym, Entry, GTAB, 0, BATCH>(a, fields, tbase, stage, ring, tab, total, nsub1, max_len1, S); break;
+        case 1: if constexpr (VecOf<Sym>::N <= 4) merge_warps<Sym, Entry, GTAB, 1, BATCH>(a, fields, tbase, stage, ring, tab, total, nsub1, max_len1, S); break;
+        case 2: merge_warps<Sym, Entry, GTAB, 2, BATCH>(a, fields, tbase, stage, ring, tab, total, nsub1, max_len1, S); break;
+        case 3: if constexpr (VecOf<Sym>::N >= 8) merge_warps<Sym, Entry, GTAB, 3, BATCH>(a, fields, tbase, stage, ring, tab, total, nsub1, max_len1, S); break;
+        default: if constexpr (VecOf<Sym>::N >= 16) merge_warps<Sym, Entry, GTAB, 4, BATCH>(a, fields, tbase, stage, ring, tab, total, nsub1, max_len1, S); break;
     }
 }
 
@@ -847,7 +894,7 @@ __global__ void __launch_bounds__(kEncCtaThreads, sizeof(Sym) == 1 ? 2 : 3) enco
     uint32_t *tbase = reinterpret_cast<uint32_t *>(reinterpret_cast<uint8_t *>(tab) + (GTAB ? 0 : a.tslots * 8ull));
     __shared__ EncShared S;
 
-    uint32_t total;
+    uint32_t total, nsub1 = 0, max_len1 = 0;
     int r;
     bool e32;
     const EncField *fields;
@@ -872,6 +919,8 @@ __global__ void __launch_bounds__(kEncCtaThreads, sizeof(Sym) == 1 ? 2 : 3) enco
         total = (uint32_t)((a.one.n + TILE - 1) / TILE);
         r = enc_clamp_r<Sym>(a.reduce_log2 >= 0 ? a.reduce_log2 : enc_rule_r(hdr->total_bits, hdr->nsymbols));
         e32 = max_len <= 23;
+        nsub1 = nsub;
+        max_len1 = max_len;
         if (threadIdx.x == 0) {
             S.f0 = a.one;
             S.f0.max_len = max_len;
@@ -903,9 +952,9 @@ __global__ void __launch_bounds__(kEncCtaThreads, sizeof(Sym) == 1 ? 2 : 3) enco
     }
     if (e32)
         merge_dispatch<Sym, uint32_t, GTAB, BATCH>(r, a, fields, tbase, stage, ring, reinterpret_cast<uint32_t *>(tab),
-                                                   total, S);
+                                                   total, nsub1, max_len1, S);
     else
-        merge_dispatch<Sym, uint64_t, GTAB, BATCH>(r, a, fields, tbase, stage, ring, tab, total, S);
+        merge_dispatch<Sym, uint64_t, GTAB, BATCH>(r, a, fields, tbase, stage, ring, tab, total, nsub1, max_len1, S);
 }
 
 }  // namespace huff
