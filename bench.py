@@ -33,7 +33,10 @@ WORKLOADS = {
     # name: (n, nbins, generator description)
     "hpc_field": (512 ** 3, 1024, "u16 Laplace(512, b=2) + 1% uniform outliers over 1024 bins, seed 1"),
     "small_field": (1 << 20, 1024, "u16 Gaussian(512, sigma=8) over 1024 bins, seed 0"),
+    "batched_fields": (None, 1024, "512 u16 fields, n log-uniform in [65536, 16777216], Laplace(512, b ~ U[0.5, 16]) "
+                                   "over 1024 bins, seed 4 (field j: stream j, size/scale from stream 10000+j)"),
 }
+BATCH_FIELDS = 512
 
 
 def make_input(name: str, n: int | None = None, rank: int = 0) -> np.ndarray:
@@ -187,13 +190,20 @@ def run_reference(args, world, rank):
     vals = []
     samp = None
     for i in range(args.warmup + args.steps):
-        gbs, samp, n, dt = oracle_leg(name, n_full, nbins, max_seconds=max(2.0, 60.0 / max(1, args.steps + args.warmup)))
+        bound = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+        if name == "batched_fields":
+            t0 = time.perf_counter()
+            gbs, samp = oracle_batched_leg(max_seconds=bound)
+            dt = time.perf_counter() - t0
+        else:
+            gbs, samp, n, dt = oracle_leg(name, n_full, nbins, max_seconds=bound)
         if i >= args.warmup:
             vals.append((gbs, dt))
     value = statistics.median(v[0] for v in vals)
     ms = statistics.median(v[1] for v in vals) * 1e3
     line = {
-        "impl": "reference", "metric": "huffman_encode_input_GBps", "value": round(value, 4), "unit": "GB/s",
+        "impl": "reference",
+        "metric": "huffman_batched_encode_input_GBps" if name == "batched_fields" else "huffman_encode_input_GBps", "value": round(value, 4), "unit": "GB/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16", "data": "synthetic",
         "config": {"workload": name, "n": n_full, "nbins": nbins, "input": desc},
@@ -334,6 +344,170 @@ def run_ours(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- batched form
+
+def batched_fields_params():
+    from paper_2010_10039_gb300 import synth
+    return [synth.batch_field_params(j) for j in range(BATCH_FIELDS)]
+
+
+def oracle_batched_leg(max_seconds: float = 15.0):
+    """The oracle (single thread) over whole fields of the batched workload,
+    taken in field order until the time bound; returns (GB/s, description)."""
+    import oracle
+    from paper_2010_10039_gb300 import synth
+    oracle.build()
+    done_bytes, dt, k = 0, 0.0, 0
+    for j, (n, b) in enumerate(batched_fields_params()):
+        if dt > max_seconds * 0.5 and k:
+            break
+        sym = synth.batch_field(j)
+        t0 = time.perf_counter()
+        h = oracle.histogram(sym, 1024)
+        book = oracle.codebook(h)
+        oracle.encode(sym, book, chunk_log2=10)
+        dt += time.perf_counter() - t0
+        done_bytes += sym.nbytes
+        k += 1
+    return done_bytes / dt / 1e9, f"fields 0..{k - 1} of the batched workload ({done_bytes // 2} symbols), " \
+                                  "histogram+codebook+encode per field, 1 thread"
+
+
+def run_batched(args, world, rank, local):
+    """512 fields, one plan (graph of histogram, codebooks, planner and one
+    persistent encode launch), against 512 separate plain calls per step."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2010_10039_gb300 as huff
+    from paper_2010_10039_gb300 import synth
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    prm = batched_fields_params()
+    fields = []
+    for j, (n, b) in enumerate(prm):
+        table = synth.cdf_table(synth.laplace_pmf(1024, 512, b))
+        sym = synth.draw_device(4, j + 100000 * rank, n, table, 2)
+        fields.append({"sym": sym, "nbins": 1024, "chunk_log2": 10,
+                       "out": torch.empty((n * 12 + 31) // 32 + 1, dtype=torch.int32, device="cuda"),
+                       "offsets": torch.empty((n >> 10) + 2, dtype=torch.int64, device="cuda"),
+                       "total_bits": torch.zeros(1, dtype=torch.int64, device="cuda")})
+    torch.cuda.synchronize()
+    total_n = sum(n for n, _ in prm)
+    in_bytes = 2 * total_n
+    t_plan = time.perf_counter()
+    plan = huff.BatchPlan(fields, autotune=True)
+    t_plan = time.perf_counter() - t_plan
+    info = plan.info()
+
+    for _ in range(args.warmup):
+        plan.encode()
+    st = plan.status()
+    if any(st):
+        raise RuntimeError(f"device status {[huff.STATUS.get(x, x) for x in st if x][:4]}")
+    K = args.steps
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    l0 = huff.huff_launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(K):
+        plan.encode()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = huff.huff_launch_count() - l0
+    clk = clocks.stop()
+    ms_step = max_over_ranks(ev0.elapsed_time(ev1) / K, world)
+    stages = plan.profile()
+    out_bytes = sum(4 * ((int(f["total_bits"].item()) + 31) // 32) for f in fields)
+    off_bytes = sum(8 * (((n + 1023) >> 10) + 1) for n, _ in prm)
+    bits = sum(int(f["total_bits"].item()) for f in fields)
+
+    # the same work as 512 separate plain calls (histogram, codebook, encode per field)
+    maxn = max(n for n, _ in prm)
+    ws = torch.zeros(huff.huff_workspace_bytes(maxn, 1024), dtype=torch.uint8, device="cuda")
+    huff.huff_workspace_init(ws)
+    hist = torch.empty(1024, dtype=torch.int32, device="cuda")
+    book = torch.empty(huff.huff_codebook_bytes(1024), dtype=torch.uint8, device="cuda")
+
+    def per_call():
+        for f in fields:
+            huff.huff_histogram(f["sym"], 1024, hist, ws)
+            huff.huff_build_codebook(hist, 1024, book, ws)
+            huff.huff_encode(f["sym"], book, 1024, f["out"], f["offsets"], f["total_bits"], ws)
+    for _ in range(max(1, args.warmup)):
+        per_call()
+    if huff.huff_get_status(ws) != 0:
+        raise RuntimeError("per-call path reported an error")
+    reps = max(1, min(K, 5))
+    ev0.record(stream)
+    for _ in range(reps):
+        per_call()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms_per_call = ev0.elapsed_time(ev1) / reps
+
+    # end to end: pinned host inputs in, encoded streams and offsets out, every step
+    host_in = [f["sym"].cpu().pin_memory() for f in fields]
+    host_out = [torch.empty_like(f["out"], device="cpu").pin_memory() for f in fields]
+    host_off = [torch.empty_like(f["offsets"], device="cpu").pin_memory() for f in fields]
+    nw = [(int(f["total_bits"].item()) + 31) // 32 for f in fields]
+    e2e_steps = max(1, min(K, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for f, h in zip(fields, host_in):
+            f["sym"].copy_(h, non_blocking=True)
+        plan.encode()
+        for f, ho, hf, w in zip(fields, host_out, host_off, nw):
+            ho[:w].copy_(f["out"][:w], non_blocking=True)
+            hf.copy_(f["offsets"], non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world)
+
+    if rank != 0:
+        return
+    peak, peak_kind = load_peak()
+    enc_alg = in_bytes + out_bytes + off_bytes
+    enc_ms = stages["encode"]
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        gbs, samp = oracle_batched_leg()
+        cpu = {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": samp}
+    value = world * in_bytes / (ms_step * 1e-3) / 1e9
+    line = {
+        "metric": "huffman_batched_encode_input_GBps",
+        "value": round(value, 3), "unit": "GB/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u16", "data": "synthetic",
+        "config": {"workload": "batched_fields", "fields": BATCH_FIELDS, "symbols": total_n, "nbins": 1024,
+                   "input": WORKLOADS["batched_fields"][2], "l2": f"inputs larger than L2 ({in_bytes >> 20} MiB per step)",
+                   "parallelism": f"replicas{world}", "avg_bits": round(bits / total_n, 4)},
+        "per_call_GBps": round(in_bytes / (ms_per_call * 1e-3) / 1e9, 3),
+        "per_call_ms": round(ms_per_call, 4),
+        "speedup_vs_per_call": round(ms_per_call / ms_step, 3),
+        "plan": {k: (round(v, 4) if isinstance(v, float) else v) for k, v in info.items()},
+        "plan_create_s": round(t_plan, 3),
+        "stages_ms_ungraphed": {k: round(v, 4) for k, v in stages.items()},
+        "roofline": {"bound": "hbm", "kernel": "batched encode (one launch, all fields)",
+                     "achieved": round(enc_alg / (enc_ms * 1e-3) / 1e9, 2), "peak": peak, "peak_kind": peak_kind,
+                     "unit": "GB/s", "frac": round(enc_alg / (enc_ms * 1e-3) / 1e9 / peak, 4), "traffic": None,
+                     "algorithmic_bytes": enc_alg},
+        "e2e": {"value": round(world * in_bytes / e2e_s / 1e9, 3), "unit": "GB/s", "h2d_bytes_per_step": in_bytes,
+                "d2h_bytes_per_step": out_bytes + off_bytes},
+        "gpu_launches": launches,
+        "cpu_baseline": cpu,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -347,6 +521,8 @@ def main():
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.workload == "batched_fields":
+        run_batched(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

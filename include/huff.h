@@ -274,6 +274,15 @@ huff_status huff_batch_plan_create(const huff_field *fields, uint32_t nfields, c
 /* Runs the whole batch: one graph launch on `stream` (asynchronous). */
 huff_status huff_batch_encode(huff_batch_plan *plan, void *stream);
 
+/*
+ * Measurement aid: runs the plan's launch sequence once on `stream` WITHOUT
+ * the graph, with events between stages, synchronises, and writes the device
+ * time in ms of each stage summed over groups: stage_ms[0] histogram,
+ * [1] codebooks, [2] tile planner (+ scratch clear), [3] encode.  The outputs
+ * are the same as huff_batch_encode's.
+ */
+huff_status huff_batch_profile(huff_batch_plan *plan, void *stream, float *stage_ms);
+
 /* Synchronises `stream` and copies each field's first device error (huff_status) into h_status[nfields]. */
 huff_status huff_batch_status(huff_batch_plan *plan, uint32_t *h_status, void *stream);
 

@@ -91,6 +91,7 @@ def lib() -> ctypes.CDLL:
                                              ctypes.POINTER(vp)]),
             "huff_batch_encode": (i32, [vp, vp]),
             "huff_batch_status": (i32, [vp, ctypes.POINTER(u32), vp]),
+            "huff_batch_profile": (i32, [vp, vp, ctypes.POINTER(ctypes.c_float)]),
             "huff_batch_get_info": (i32, [vp, ctypes.POINTER(huff_batch_info)]),
             "huff_batch_codebook": (vp, [vp, u32]),
             "huff_batch_histogram": (vp, [vp, u32]),
@@ -335,6 +336,12 @@ class BatchPlan:
 
     def encode(self, stream=None) -> None:
         _check(lib().huff_batch_encode(self.handle, _stream(stream)), "huff_batch_encode")
+
+    def profile(self, stream=None) -> dict:
+        """One run without the graph, with per-stage device times (ms)."""
+        ms = (ctypes.c_float * 4)()
+        _check(lib().huff_batch_profile(self.handle, _stream(stream), ms), "huff_batch_profile")
+        return {"histogram": ms[0], "codebook": ms[1], "plan": ms[2], "encode": ms[3]}
 
     def status(self, stream=None) -> list[int]:
         st = (ctypes.c_uint32 * self.n)()

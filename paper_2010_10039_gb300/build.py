@@ -1,5 +1,7 @@
 """Builds libhuff.so in-tree for sm_103a with nvcc (one object per .cu/.cpp
-source, compiled in parallel, then linked into one shared library)."""
+source, compiled in parallel, then linked into one shared library), and
+libhuffsynth.so, the device copy of the seeded input generator that the
+benchmark and the tests use (not part of libhuff)."""
 from __future__ import annotations
 
 import glob
@@ -15,6 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libhuff.so")
+SYNTH_SRC = os.path.join(HERE, "synthgen", "synthgen.cu")
+SYNTH_LIB = os.path.join(HERE, "libhuffsynth.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -58,13 +62,17 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
         if verbose and (r.stdout or r.stderr):
             sys.stderr.write(r.stdout + r.stderr)
 
+    synth_obj = os.path.join(BUILD, "synthgen.cu.o")
+    if force or _stale(synth_obj, SYNTH_SRC, [os.path.abspath(__file__)]):
+        jobs.append([nvcc] + flags + ["-x", "cu", "-c", SYNTH_SRC, "-o", synth_obj])
     if jobs:
         with ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
             list(ex.map(run, jobs))
-    if jobs or not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
-        tmp = LIB + f".tmp{os.getpid()}"
-        run([nvcc, "-shared"] + ARCH + ["-o", tmp] + objs + ["-lpthread"])
-        os.replace(tmp, LIB)
+    for lib, lib_objs in ((LIB, objs), (SYNTH_LIB, [synth_obj])):
+        if not os.path.exists(lib) or any(os.path.getmtime(o) > os.path.getmtime(lib) for o in lib_objs):
+            tmp = lib + f".tmp{os.getpid()}"
+            run([nvcc, "-shared"] + ARCH + ["-o", tmp] + lib_objs + ["-lpthread"])
+            os.replace(tmp, lib)
     return LIB
 
 

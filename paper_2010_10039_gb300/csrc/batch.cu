@@ -106,14 +106,18 @@ huff_status apply_chunks(huff_batch_plan *p, int auto_m) {
 }
 
 // The launch set of one batch run, enqueued on st (captured into the graph).
-huff_status record(huff_batch_plan *p, const Setting &s, cudaStream_t st) {
+// With ev (5 events per group), events are recorded around each stage.
+huff_status record(huff_batch_plan *p, const Setting &s, cudaStream_t st, const cudaEvent_t *ev = nullptr) {
     if (cudaMemsetAsync(p->dmem + p->off_status, 0, 4 * p->fields.size(), st) != cudaSuccess) return HUFF_ERR_CUDA;
     if (p->hist_bytes && cudaMemsetAsync(p->dmem + p->off_hist0, 0, p->hist_bytes, st) != cudaSuccess)
         return HUFF_ERR_CUDA;
     const int sms = sm_count();
+    int gi = 0;
+    auto mark = [&](int k) { return ev ? cudaEventRecord(ev[5 * gi + k], st) == cudaSuccess : true; };
     for (BatchGroup &g : p->groups) {
         const uint32_t nf = (uint32_t)g.idx.size();
         huff_status e;
+        if (!mark(0)) return HUFF_ERR_CUDA;
         if (!g.tiles.empty()) {
             e = histogram_batch_launch(g.dtype, reinterpret_cast<const HistTile *>(p->dmem + g.off_tiles),
                                        (uint32_t)g.tiles.size(),
@@ -121,18 +125,23 @@ huff_status record(huff_batch_plan *p, const Setting &s, cudaStream_t st) {
                                        g.grid_h, st);
             if (e != HUFF_OK) return e;
         }
+        if (!mark(1)) return HUFF_ERR_CUDA;
         e = codebook_batch_launch(reinterpret_cast<const CbArgs *>(p->dmem + g.off_cb), nf, g.max_nbins, g.grid_c,
                                   g.cbscr_stride ? p->dmem + g.off_cbscr : nullptr, g.cbscr_stride, st);
         if (e != HUFF_OK) return e;
         EncField *ef = reinterpret_cast<EncField *>(p->dmem + g.off_ef);
         EncBatchConf *conf = reinterpret_cast<EncBatchConf *>(p->dmem + g.off_conf);
+        if (!mark(2)) return HUFF_ERR_CUDA;
         e = encode_batch_plan_launch(g.dtype, ef, nf, conf, s.r, (uint32_t)s.max_subtiles, st);
         if (e != HUFF_OK) return e;
         if (cudaMemsetAsync(p->dmem + g.off_escr, 0, g.escr_bytes, st) != cudaSuccess) return HUFF_ERR_CUDA;
         int c = s.ctas_per_sm <= 0 ? g.enc_occ : std::min(s.ctas_per_sm, g.enc_occ);
         if (c < 1) c = 1;
+        if (!mark(3)) return HUFF_ERR_CUDA;
         e = encode_batch_launch(g.dtype, ef, nf, conf, g.max_nbins, p->dmem + g.off_escr, (uint32_t)(sms * c), st);
         if (e != HUFF_OK) return e;
+        if (!mark(4)) return HUFF_ERR_CUDA;
+        gi++;
     }
     return HUFF_OK;
 }
@@ -426,6 +435,30 @@ huff_status huff_batch_encode(huff_batch_plan *p, void *stream) {
     if (cudaGraphLaunch(p->exec, (cudaStream_t)stream) != cudaSuccess) return HUFF_ERR_CUDA;
     note_launch((int)p->kernels_per_run);
     return HUFF_OK;
+}
+
+huff_status huff_batch_profile(huff_batch_plan *p, void *stream, float *stage_ms) {
+    if (!p || !stage_ms) return HUFF_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<cudaEvent_t> ev(5 * p->groups.size(), nullptr);
+    huff_status e = HUFF_OK;
+    for (auto &x : ev)
+        if (cudaEventCreate(&x) != cudaSuccess) { x = nullptr; e = HUFF_ERR_CUDA; }
+    if (e == HUFF_OK) e = record(p, p->cur, st, ev.data());
+    if (e == HUFF_OK && cudaStreamSynchronize(st) != cudaSuccess) e = HUFF_ERR_CUDA;
+    for (int k = 0; k < 4; k++) stage_ms[k] = 0.f;
+    for (size_t g = 0; g < p->groups.size() && e == HUFF_OK; g++)
+        for (int k = 0; k < 4; k++) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, ev[5 * g + k], ev[5 * g + k + 1]) != cudaSuccess) {
+                e = HUFF_ERR_CUDA;
+                break;
+            }
+            stage_ms[k] += ms;
+        }
+    for (auto &x : ev)
+        if (x) cudaEventDestroy(x);
+    return e;
 }
 
 huff_status huff_batch_status(huff_batch_plan *p, uint32_t *h_status, void *stream) {

@@ -230,3 +230,45 @@ def empirical_bits(pmf: np.ndarray) -> float:
     p = np.asarray(pmf, dtype=np.float64)
     p = p[p > 0]
     return float(-(p * np.log2(p)).sum())
+
+
+# ----------------------------------------------------------------------------
+# the same draws on the GPU (libhuffsynth.so, built next to libhuff.so)
+# ----------------------------------------------------------------------------
+
+_synth_lib = None
+
+
+def _synthgen():
+    global _synth_lib
+    if _synth_lib is None:
+        import ctypes
+        path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libhuffsynth.so")
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is not built (paper_2010_10039_gb300/build.py builds it)")
+        L = ctypes.CDLL(path)
+        L.synth_draw.restype = ctypes.c_int
+        L.synth_draw.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p, ctypes.c_uint32,
+                                 ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p]
+        _synth_lib = L
+    return _synth_lib
+
+
+def draw_device(seed: int, stream: int, n: int, table, width: int, mapping=None, out=None, start: int = 0):
+    """``draw`` on the current CUDA device: returns (or fills) a torch tensor of
+    n symbols (uint8 / int16 / int32 storage for widths 1 / 2 / 4) equal bit for
+    bit to ``draw(seed, stream, n, table, width, mapping)[start:]``."""
+    import torch
+    tdt = {1: torch.uint8, 2: torch.int16, 4: torch.int32}[width]
+    if out is None:
+        out = torch.empty(n, dtype=tdt, device="cuda")
+    t = torch.from_numpy(np.ascontiguousarray(table, dtype=np.uint64).view(np.int64)).cuda()
+    mp = None
+    if mapping is not None:
+        mp = torch.from_numpy(np.asarray(mapping).astype(np.uint32).view(np.int32)).cuda()
+    rc = _synthgen().synth_draw(out.data_ptr() if n else None, n, width, t.data_ptr(), len(table),
+                                mp.data_ptr() if mp is not None else None, seed, stream, start,
+                                torch.cuda.current_stream().cuda_stream)
+    if rc != 0:
+        raise RuntimeError(f"synth_draw failed with CUDA error {rc}")
+    return out
