@@ -298,6 +298,86 @@ int huff_batch_chunk_log2(const huff_batch_plan *plan, uint32_t field);
 /* Frees the plan after synchronising the device work it may still have in flight. */
 void huff_batch_plan_destroy(huff_batch_plan *plan);
 
+/* ------------------------------------------------------------------------
+ * Served form (no paper counterpart): a request loop on one GPU.  Clients
+ * submit encode jobs whose symbols are already in device memory; a
+ * dispatcher thread admits them in arrival order while the server's device
+ * memory budget and in-flight limit allow, and launches every group of
+ * admitted jobs as one batch (the batched histogram, codebook, planner and
+ * encode kernels) on the next free stream context, so jobs that arrive while
+ * others run are batched and overlap with them on the device (continuous
+ * batching).  Each job's codebook, stream and chunk offsets are written to
+ * server memory that stays valid until the client releases the ticket.
+ * Results are identical to the plain calls on the same input.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    uint64_t mem_budget_bytes;   /* device memory for job results (codebook, stream, offsets)          */
+    uint32_t max_inflight;       /* jobs admitted and not yet released (0 = 4096)                      */
+    uint32_t nstreams;           /* batches that may run at once, one stream each (0 = 2)               */
+    uint32_t max_batch;          /* jobs per batch (1..512, 0 = 64)                                     */
+    int32_t chunk_log2;          /* M of every job (0 = 10)                                             */
+    uint64_t max_batch_symbols;  /* symbols per batch (0 = 2^31)                                        */
+    uint32_t max_queue;          /* jobs waiting for admission before submit returns BUSY (0 = 1<<20)   */
+    uint32_t reserved;
+} huff_serve_cfg;
+
+typedef struct {
+    const void *d_sym;           /* n symbols of dtype in device memory, element aligned; must stay
+                                    unchanged until the job is done                                  */
+    uint64_t n;                  /* 1 .. max_batch_symbols                                            */
+    huff_dtype dtype;
+    uint32_t nbins;
+} huff_request;
+
+typedef struct {
+    huff_status status;          /* HUFF_OK or the job's first device error (or CANCELLED)            */
+    int32_t chunk_log2;
+    uint64_t total_bits;
+    const uint32_t *d_out;       /* ceil(total_bits / 32) words (server memory)                       */
+    const uint64_t *d_chunk_bit_offset;   /* ceil(n / 2^M) + 1 offsets (server memory)               */
+    const void *d_codebook;      /* the job's codebook (layout above, server memory)                  */
+    double t_submit, t_admit, t_launch, t_done;   /* seconds on the server's steady clock             */
+} huff_result;
+
+typedef struct {
+    uint64_t submitted, completed, cancelled, batches;
+    uint64_t max_batch_jobs;     /* largest batch launched                                            */
+    uint32_t max_concurrent_batches;   /* most batches on the device at once                        */
+    uint32_t reserved;
+    uint64_t pool_used, pool_peak, pool_capacity;
+    uint64_t symbols_done;
+} huff_serve_stats;
+
+typedef struct huff_server huff_server;
+
+void huff_serve_default_cfg(huff_serve_cfg *cfg);
+
+/* Creates the server on the current device: allocates the budget and the stream contexts. */
+huff_status huff_serve_create(const huff_serve_cfg *cfg, huff_server **out);
+
+/*
+ * Queues a job; *ticket identifies it.  HUFF_ERR_INVALID_ARG for a bad
+ * request, HUFF_ERR_OOM if its results could never fit the budget,
+ * HUFF_ERR_BUSY if the admission queue is full (nothing queued).
+ */
+huff_status huff_serve_submit(huff_server *srv, const huff_request *req, uint64_t *ticket);
+
+/* HUFF_OK and *res if the job is done (or cancelled); HUFF_ERR_BUSY while it is
+   pending; HUFF_ERR_NOT_FOUND for an unknown or released ticket. */
+huff_status huff_serve_poll(huff_server *srv, uint64_t ticket, huff_result *res);
+
+/* Blocks until the job is done (or cancelled), then as huff_serve_poll. */
+huff_status huff_serve_wait(huff_server *srv, uint64_t ticket, huff_result *res);
+
+/* Frees the job's result memory; its result pointers become invalid.  A job
+   still pending is released as soon as it completes. */
+huff_status huff_serve_release(huff_server *srv, uint64_t ticket);
+
+huff_status huff_serve_get_stats(huff_server *srv, huff_serve_stats *stats);
+
+/* Cancels jobs not yet launched, waits for the launched ones, frees everything. */
+huff_status huff_serve_destroy(huff_server *srv);
+
 /* Synchronises `stream` and returns the first device error recorded in d_ws. */
 huff_status huff_get_status(const void *d_ws, void *stream);
 

@@ -58,6 +58,32 @@ class huff_batch_info(ctypes.Structure):
                 ("candidates", ctypes.c_uint32), ("tuned_ms", ctypes.c_float), ("device_bytes", ctypes.c_uint64)]
 
 
+class huff_serve_cfg(ctypes.Structure):
+    _fields_ = [("mem_budget_bytes", ctypes.c_uint64), ("max_inflight", ctypes.c_uint32),
+                ("nstreams", ctypes.c_uint32), ("max_batch", ctypes.c_uint32), ("chunk_log2", ctypes.c_int32),
+                ("max_batch_symbols", ctypes.c_uint64), ("max_queue", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class huff_request(ctypes.Structure):
+    _fields_ = [("d_sym", ctypes.c_void_p), ("n", ctypes.c_uint64), ("dtype", ctypes.c_int32),
+                ("nbins", ctypes.c_uint32)]
+
+
+class huff_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("chunk_log2", ctypes.c_int32), ("total_bits", ctypes.c_uint64),
+                ("d_out", ctypes.c_void_p), ("d_chunk_bit_offset", ctypes.c_void_p), ("d_codebook", ctypes.c_void_p),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_launch", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
+
+
+class huff_serve_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("cancelled", ctypes.c_uint64),
+                ("batches", ctypes.c_uint64), ("max_batch_jobs", ctypes.c_uint64),
+                ("max_concurrent_batches", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("pool_used", ctypes.c_uint64), ("pool_peak", ctypes.c_uint64), ("pool_capacity", ctypes.c_uint64),
+                ("symbols_done", ctypes.c_uint64)]
+
+
 _lib = None
 
 
@@ -97,6 +123,14 @@ def lib() -> ctypes.CDLL:
             "huff_batch_histogram": (vp, [vp, u32]),
             "huff_batch_chunk_log2": (i32, [vp, u32]),
             "huff_batch_plan_destroy": (None, [vp]),
+            "huff_serve_default_cfg": (None, [ctypes.POINTER(huff_serve_cfg)]),
+            "huff_serve_create": (i32, [ctypes.POINTER(huff_serve_cfg), ctypes.POINTER(vp)]),
+            "huff_serve_submit": (i32, [vp, ctypes.POINTER(huff_request), ctypes.POINTER(u64)]),
+            "huff_serve_poll": (i32, [vp, u64, ctypes.POINTER(huff_result)]),
+            "huff_serve_wait": (i32, [vp, u64, ctypes.POINTER(huff_result)]),
+            "huff_serve_release": (i32, [vp, u64]),
+            "huff_serve_get_stats": (i32, [vp, ctypes.POINTER(huff_serve_stats)]),
+            "huff_serve_destroy": (i32, [vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -392,3 +426,77 @@ def device_view(ptr: int, nbytes: int):
     (valid while the owner lives)."""
     torch = _torch()
     return torch.as_tensor(_DeviceBytes(ptr, nbytes), device="cuda")
+
+
+# ------------------------------------------------------------------ served form
+
+class Server:
+    """huff_server: submit device-resident symbol tensors, wait for results.
+    Keyword arguments are huff_serve_cfg fields (mem_budget_bytes, nstreams,
+    max_batch, max_inflight, chunk_log2, max_batch_symbols, max_queue)."""
+
+    def __init__(self, **cfg):
+        c = huff_serve_cfg()
+        lib().huff_serve_default_cfg(ctypes.byref(c))
+        for k, v in cfg.items():
+            setattr(c, k, int(v))
+        h = ctypes.c_void_p()
+        _check(lib().huff_serve_create(ctypes.byref(c), ctypes.byref(h)), "huff_serve_create")
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, sym, nbins: int, keep: bool = True) -> int:
+        """Queues an encode of the 1-D integer tensor `sym`; returns the ticket.
+        The tensor is kept alive until the ticket is released (keep=True)."""
+        r = huff_request(_ptr(sym), sym.numel(), dtype_code(sym), nbins)
+        t = ctypes.c_uint64()
+        rc = lib().huff_serve_submit(self.handle, ctypes.byref(r), ctypes.byref(t))
+        _check(rc, "huff_serve_submit")
+        if keep:
+            self._keep[t.value] = sym
+        return t.value
+
+    def submit_raw(self, ptr: int, n: int, dtype: int, nbins: int) -> tuple[int, int]:
+        """Like submit for a raw device pointer; returns (status, ticket)."""
+        r = huff_request(ptr, n, dtype, nbins)
+        t = ctypes.c_uint64()
+        rc = lib().huff_serve_submit(self.handle, ctypes.byref(r), ctypes.byref(t))
+        return rc, t.value
+
+    @staticmethod
+    def _res(r: huff_result) -> dict:
+        return {k: getattr(r, k) for k, _ in huff_result._fields_}
+
+    def poll(self, ticket: int):
+        r = huff_result()
+        rc = lib().huff_serve_poll(self.handle, ticket, ctypes.byref(r))
+        if rc == STATUS_CODE["HUFF_ERR_BUSY"]:
+            return None
+        _check(rc, "huff_serve_poll")
+        return self._res(r)
+
+    def wait(self, ticket: int) -> dict:
+        r = huff_result()
+        _check(lib().huff_serve_wait(self.handle, ticket, ctypes.byref(r)), "huff_serve_wait")
+        return self._res(r)
+
+    def release(self, ticket: int) -> None:
+        _check(lib().huff_serve_release(self.handle, ticket), "huff_serve_release")
+        self._keep.pop(ticket, None)
+
+    def stats(self) -> dict:
+        st = huff_serve_stats()
+        _check(lib().huff_serve_get_stats(self.handle, ctypes.byref(st)), "huff_serve_get_stats")
+        return {k: getattr(st, k) for k, _ in huff_serve_stats._fields_}
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            lib().huff_serve_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
