@@ -225,6 +225,51 @@ def batch_field(j: int, seed: int = 4, K: int = 1024, n_scale: float = 1.0) -> n
     return draw(seed, j, n, cdf_table(laplace_pmf(K, K // 2, b)), 2)
 
 
+# ----------------------------------------------------------------------------
+# served workload: Poisson arrivals of mixed requests
+# ----------------------------------------------------------------------------
+
+_ZIPF_256_TABLE = None
+_SERVED_EDGES = np.arange(1024, dtype=np.float64) + 0.5 - 512.0
+
+
+def served_arrivals(count: int, rate: float = 2000.0, seed: int = 5) -> np.ndarray:
+    """Arrival times (s, from 0) of the first `count` requests: exponential
+    gaps of mean 1/rate from stream 2 (inverse CDF of the uniform draws)."""
+    u = (u64_range(seed, 2, 0, count) >> np.uint64(11)).astype(np.float64) / float(1 << 53)
+    return np.cumsum(-np.log1p(-u) / rate)
+
+
+def served_request(i: int, seed: int = 5, n_lo: int = 16384, n_hi: int = 67108864):
+    """Request i of the served workload as (width, n, nbins, table): half u8
+    Zipf(1.2) over 256 ids, half u16 over 1024 bins from a discretised
+    Gaussian or Laplace centred at 512 with sigma / b log-uniform in [1, 64];
+    n log-uniform in [n_lo, n_hi].  Its symbols are draw(seed, 100 + i, n,
+    table, width).  Parameters come from stream 1,000,000 + i."""
+    global _ZIPF_256_TABLE
+    u = [u64_scalar(seed, 1_000_000 + i, k) / 2.0 ** 64 for k in range(4)]
+    n = int(round(math.exp(math.log(n_lo) + u[0] * (math.log(n_hi) - math.log(n_lo)))))
+    if u[1] < 0.5:
+        if _ZIPF_256_TABLE is None:
+            _ZIPF_256_TABLE = cdf_table(zipf_pmf(256, 1.2))
+        return 1, n, 256, _ZIPF_256_TABLE
+    scale = math.exp(u[2] * math.log(64.0))
+    edges = _SERVED_EDGES
+    if u[3] < 0.5:
+        from scipy.special import ndtr
+        cdf = ndtr(edges / scale)
+    else:
+        cdf = np.where(edges < 0, 0.5 * np.exp(edges / scale), 1.0 - 0.5 * np.exp(-edges / scale))
+    cdf[-1] = 1.0
+    return 2, n, 1024, cdf_table(np.diff(np.concatenate([[0.0], cdf])))
+
+
+def served_symbols(i: int, seed: int = 5, **kw) -> np.ndarray:
+    """The symbols of served request i, drawn on the host (for the oracle)."""
+    width, n, nbins, table = served_request(i, seed, **kw)
+    return draw(seed, 100 + i, n, table, width)
+
+
 def empirical_bits(pmf: np.ndarray) -> float:
     """Shannon entropy of a pmf in bits (diagnostics only)."""
     p = np.asarray(pmf, dtype=np.float64)
