@@ -51,7 +51,7 @@ constexpr uint64_t kFlagAgg = 1ull << 62;
 constexpr uint64_t kFlagPre = 2ull << 62;
 constexpr uint64_t kValMask = (1ull << 62) - 1;
 constexpr uint64_t kAggLenMask = (1ull << 24) - 1;
-constexpr uint32_t kBad32 = 1u << 23;      // u32 table entry flag: symbol without codeword
+constexpr uint32_t kBad32 = 1u << 5;       // flag of a position without codeword (bit 5 is free in u32 entries)
 constexpr int kEncCtaThreads = kEncThreads + 64;   // merge warps + look-back warp + write-out warp
 
 struct EncArgs {
@@ -105,15 +105,21 @@ __device__ __forceinline__ void sym_from_vec(const uint4 &v, uint32_t *s, uint32
 }
 
 // ---------------------------------------------------------------- codebook entries
-// u32 form (codewords up to 23 bits): len << 24 | code, kBad32 for no codeword.
+// u32 form (codewords up to 23 bits): the code left-aligned in the top l bits
+// and the length l in bits 0..4, e = code << (32 - l) | l; kBad32 for no
+// codeword, 0 for padding.  A funnel shift uses only the low 5 bits of its
+// shift operand, so funnelshift_l(e, lo, e) = (lo << l) | code appends the
+// codeword to a word in one instruction, funnelshift_l(lo, hi, e) carries into
+// the high word, and a sum of entries keeps the sum of lengths in bits 0..8
+// (codes start at bit 9 or higher).
 // u64 form: the codebook's cw (len << 58 | code), 0 for no codeword.
 
 template <typename Entry>
 __device__ __forceinline__ Entry entry_from_cw(uint64_t c);
 template <>
 __device__ __forceinline__ uint32_t entry_from_cw<uint32_t>(uint64_t c) {
-    uint32_t l = (uint32_t)(c >> HUFF_CW_LEN_SHIFT);
-    return l ? ((l << 24) | (uint32_t)(c & 0x7FFFFFu)) : kBad32;
+    const uint32_t l = (uint32_t)(c >> HUFF_CW_LEN_SHIFT);
+    return l ? (((uint32_t)c << (32 - l)) | l) : kBad32;
 }
 template <>
 __device__ __forceinline__ uint64_t entry_from_cw<uint64_t>(uint64_t c) { return c; }
@@ -121,14 +127,17 @@ __device__ __forceinline__ uint64_t entry_from_cw<uint64_t>(uint64_t c) { return
 template <typename Entry>
 __device__ __forceinline__ uint32_t ent_len(Entry e);
 template <>
-__device__ __forceinline__ uint32_t ent_len<uint32_t>(uint32_t e) { return e >> 24; }
+__device__ __forceinline__ uint32_t ent_len<uint32_t>(uint32_t e) { return e & 31u; }
 template <>
 __device__ __forceinline__ uint32_t ent_len<uint64_t>(uint64_t e) { return (uint32_t)(e >> HUFF_CW_LEN_SHIFT); }
 
 template <typename Entry>
 __device__ __forceinline__ uint64_t ent_code(Entry e);
 template <>
-__device__ __forceinline__ uint64_t ent_code<uint32_t>(uint32_t e) { return e & 0x7FFFFFu; }
+__device__ __forceinline__ uint64_t ent_code<uint32_t>(uint32_t e) {
+    const uint32_t l = e & 31u;
+    return l ? (e >> (32 - l)) : 0u;
+}
 template <>
 __device__ __forceinline__ uint64_t ent_code<uint64_t>(uint64_t e) { return e & ((1ull << HUFF_CW_LEN_SHIFT) - 1); }
 
@@ -160,18 +169,9 @@ __device__ __forceinline__ bool vec_out_of_table(const uint4 &v, uint32_t tmask,
     return ((v.x | v.y | v.z | v.w) & ~tmask) != 0;
 }
 
-// acc = acc (+) codeword: append l bits (one step of reduce-merge).
-template <typename Entry>
-__device__ __forceinline__ void concat(uint64_t &acc, Entry e, uint32_t l) {
-    if (sizeof(Entry) == 4) {
-        // l <= 23: a 32-bit funnel shift makes the high word, no 64-bit shift
-        uint32_t lo = (uint32_t)acc, hi = (uint32_t)(acc >> 32);
-        hi = __funnelshift_l(lo, hi, l);
-        lo = (lo << l) | (uint32_t)ent_code<Entry>(e);
-        acc = ((uint64_t)hi << 32) | lo;
-    } else {
-        acc = (acc << l) | ent_code<Entry>(e);
-    }
+// acc = acc (+) codeword of a u64 entry: append l bits (one step of reduce-merge).
+__device__ __forceinline__ void concat64(uint64_t &acc, uint64_t e, uint32_t l) {
+    acc = (acc << l) | ent_code<uint64_t>(e);
 }
 
 // ---------------------------------------------------------------- bit ring
@@ -454,22 +454,38 @@ __device__ __forceinline__ uint32_t merge_vec(const uint32_t *sv, uint32_t valid
     uint32_t tot = 0;
 #pragma unroll
     for (int r = 0; r < NR; r++) {
-        uint64_t ac = 0;
-        uint32_t bb = 0;
+        if constexpr (sizeof(Entry) == 4) {
+            // lo/hi: the run so far; esum: sum of entries (lengths in bits 0..8)
+            uint32_t lo = 0, hi = 0, esum = 0;
 #pragma unroll
-        for (int x = 0; x < RL; x++) {
-            const int xi = r * RL + x;
-            Entry en = table_get<Entry, GTAB>(tab, gcw, sv[xi], nbins, tmask);
-            if (!FULL && xi >= (int)valid) en = (Entry)0;            // padding past n: length 0
-            else if (sizeof(Entry) == 4) bad |= (uint32_t)en;
-            else bad |= en == 0 ? kBad32 : 0u;
-            const uint32_t l = ent_len<Entry>(en);
-            concat<Entry>(ac, en, l);
-            bb += l;
+            for (int x = 0; x < RL; x++) {
+                const int xi = r * RL + x;
+                uint32_t en = (uint32_t)table_get<Entry, GTAB>(tab, gcw, sv[xi], nbins, tmask);
+                if (!FULL && xi >= (int)valid) en = 0u;               // padding past n: length 0
+                bad |= en;
+                hi = __funnelshift_l(lo, hi, en);
+                lo = __funnelshift_l(en, lo, en);
+                esum += en;
+            }
+            acc[r] = ((uint64_t)hi << 32) | lo;
+            rb[r] = esum & 511u;
+        } else {
+            uint64_t ac = 0;
+            uint32_t bb = 0;
+#pragma unroll
+            for (int x = 0; x < RL; x++) {
+                const int xi = r * RL + x;
+                Entry en = table_get<Entry, GTAB>(tab, gcw, sv[xi], nbins, tmask);
+                if (!FULL && xi >= (int)valid) en = (Entry)0;        // padding past n: length 0
+                else bad |= en == 0 ? kBad32 : 0u;
+                const uint32_t l = ent_len<Entry>(en);
+                concat64(ac, en, l);
+                bb += l;
+            }
+            acc[r] = ac;
+            rb[r] = bb;
         }
-        acc[r] = ac;
-        rb[r] = bb;
-        tot += bb;
+        tot += rb[r];
     }
     return tot;
 }
