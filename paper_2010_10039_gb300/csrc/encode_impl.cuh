@@ -343,7 +343,7 @@ __device__ __forceinline__ void produce_next(const EncArgs &a, const EncField *f
     constexpr uint32_t SUB = enc_sub_syms<Sym>();
     if (p.sub >= p.nsub && p.tile < total) {
         p.tile = p.next;
-        p.next = p.tile < total ? atomicAdd(a.tile_counter, 1u) : p.tile;
+        if (p.tile < total) p.next = atomicAdd(a.tile_counter, 1u);   // predicated: not waited on here
         p.sub = 0;
         if (p.tile < total) {
             p.f = BATCH ? field_of(tbase, a.nfields, p.tile) : 0u;
@@ -386,7 +386,9 @@ __device__ __forceinline__ void produce_next_one(const EncArgs &a, ProducerOne &
     constexpr uint32_t SUB = enc_sub_syms<Sym>();
     if (p.sub >= nsub && p.tile < total) {
         p.tile = p.next;
-        p.next = p.tile < total ? atomicAdd(a.tile_counter, 1u) : p.tile;
+        // predicated, not selected: nothing reads the new id before the next
+        // tile switch, so the atomic's round trip does not stall the warp
+        if (p.tile < total) p.next = atomicAdd(a.tile_counter, 1u);
         p.sub = 0;
     }
     const int s = (int)(p.slot % kEncStages);
@@ -535,7 +537,7 @@ __device__ void merge_warps(const EncArgs &a, const EncField *fields, const uint
             prod.next = atomicAdd(a.tile_counter, 1u);
         } else {
             one.next = atomicAdd(a.tile_counter, 1u);
-            stage_field[0] = stage_field[1] = stage_field[2] = stage_field[3] = 0;
+            for (int i = 0; i < kEncStages; i++) stage_field[i] = 0;
         }
         for (int i = 0; i < kEncStages; i++) {
             if (BATCH) produce_next<Sym, true>(a, fields, tbase, prod, total, stage, S.bars, stage_tile, stage_field);
@@ -731,7 +733,6 @@ __device__ void merge_warps(const EncArgs &a, const EncField *fields, const uint
             mbar_arrive(&S.full[sl]);
         }
         base += (L + 31) / 32;
-        merge_sync();                                      // stage_tile of the next tile written
     }
 }
 
