@@ -231,7 +231,7 @@ def run_ours(args, world, rank, local):
     n, nbins, desc = WORKLOADS[name]
     sym_np = make_input(name, n, rank)
     sym = torch.from_numpy(sym_np.view(np.int16)).cuda()
-    params = {"chunk_log2": args.chunk_log2}
+    params = {"chunk_log2": args.chunk_log2, "merge": {"scan": 1, "shuffle": 2}[args.merge]}
     pipe = huff.Pipeline(n, nbins, params)
     stream = torch.cuda.current_stream()
 
@@ -327,14 +327,16 @@ def run_ours(args, world, rank, local):
         "dtype": "u16",
         "data": "synthetic",
         "config": {"workload": name, "n": n, "nbins": nbins, "input": desc, "chunk_log2": args.chunk_log2,
+                   "encode_layout": args.merge,
                    "l2": "inputs larger than L2 (268 MB per step)", "parallelism": f"replicas{world}",
                    "avg_bits": round(total_bits / n, 4)},
         "stages_ms": {"histogram": round(hist_ms, 5), "codebook": round(cb_ms, 5), "encode": round(enc_ms, 5)},
         "encode_only_GBps": round(in_bytes / enc_s / 1e9, 3),
-        "roofline": {"bound": "hbm", "kernel": "encode (a4-a6)", "achieved": round(enc_alg / enc_s / 1e9, 2),
+        "roofline": {"bound": "hbm", "kernel": "encode (a4-a6)" if args.merge == "scan" else
+                     "encode, paper layout: merge + scan + gather kernels", "achieved": round(enc_alg / enc_s / 1e9, 2),
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": round(enc_alg / enc_s / 1e9 / peak, 4),
-                     "traffic": load_traffic("encode_kernel") if name == "hpc_field" else None,
+                     "traffic": load_traffic("encode_kernel") if name == "hpc_field" and args.merge == "scan" else None,
                      "algorithmic_bytes": enc_alg},
         "roofline_histogram": {"bound": "hbm", "achieved": round(hist_alg / (hist_ms * 1e-3) / 1e9, 2),
                                "peak": peak, "unit": "GB/s",
@@ -776,6 +778,8 @@ def main():
     ap.add_argument("--workload", default="hpc_field", choices=sorted(WORKLOADS))
     ap.add_argument("--chunk-log2", dest="chunk_log2", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--merge", default="scan", choices=["scan", "shuffle"],
+                    help="encode layout: fused single pass (scan) or the paper's three kernels (shuffle)")
     ap.add_argument("--rate", type=float, default=2000.0, help="served: arrivals per second")
     ap.add_argument("--duration", type=float, default=60.0, help="served: seconds of arrivals")
     ap.add_argument("--saturation-requests", type=int, default=1000, help="served: closed-loop requests")

@@ -98,9 +98,14 @@ typedef struct {
 } huff_params;
 
 enum {
-    HUFF_MERGE_AUTO = 0,
-    HUFF_MERGE_SCAN = 1,     /* block scan of merged lengths, one scatter into shared memory  */
-    HUFF_MERGE_SHUFFLE = 2   /* the paper's log-step shuffle-merge in shared memory           */
+    HUFF_MERGE_AUTO = 0,     /* = HUFF_MERGE_SCAN                                                */
+    HUFF_MERGE_SCAN = 1,     /* one fused kernel: scan of merged lengths, one placement in shared
+                                memory, decoupled look-back and write-out of the dense stream      */
+    HUFF_MERGE_SHUFFLE = 2   /* the paper's layout: per chunk of 2^M symbols, reduce-merge and
+                                M - r log steps of shuffle-merge in shared memory into a chunk
+                                slot of the workspace, then a scan of chunk lengths and a
+                                coalescing copy (three kernels).  Needs r <= 4 (-1 = 3) and
+                                M - r <= 10, and a workspace sized with these parameters      */
 };
 
 /* Fills *p with the defaults (M = 10, r = auto, block = 0, merge = auto). */

@@ -103,8 +103,12 @@ uint64_t huff_max_output_words(uint64_t n, uint32_t max_len) {
     return (n * (uint64_t)max_len + 31) / 32;
 }
 
-size_t huff_workspace_bytes(uint64_t n, uint32_t nbins, const huff_params *) {
+size_t huff_workspace_bytes(uint64_t n, uint32_t nbins, const huff_params *p) {
     size_t a = encode_scratch_bytes(n);
+    if (p && p->merge == HUFF_MERGE_SHUFFLE && p->chunk_log2 >= 4 && p->chunk_log2 <= 30) {
+        const size_t b = shuffle_scratch_bytes(n, p->chunk_log2, p->reduce_log2);
+        if (b > a) a = b;
+    }
     size_t b = codebook_scratch_bytes(nbins);
     size_t s = a > b ? a : b;
     return kWsHeaderBytes + ((s + 255) & ~size_t(255));
@@ -151,6 +155,10 @@ huff_status huff_encode(const void *d_sym, uint64_t n, huff_dtype dtype, const v
         if (cudaMemsetAsync(d_total_bits, 0, 8, st) != cudaSuccess) return HUFF_ERR_CUDA;
         return HUFF_OK;
     }
+    if (prm.merge == HUFF_MERGE_SHUFFLE)
+        return encode_shuffle_launch(d_sym, n, dtype, d_codebook, nbins, prm.chunk_log2, prm.reduce_log2, 48, d_out,
+                                     out_capacity_words, d_chunk_bit_offset, d_total_bits, scratch_of(d_ws),
+                                     status_of(d_ws), st);
     return encode_launch(d_sym, n, dtype, d_codebook, nbins, prm.chunk_log2, prm.reduce_log2, d_out, out_capacity_words,
                          d_chunk_bit_offset, d_total_bits, scratch_of(d_ws), status_of(d_ws), st);
 }

@@ -77,6 +77,18 @@ __device__ inline CbArrays cb_carve(uint8_t *p, uint32_t nbins) {
     return a;
 }
 
+// Bitonic stages of stride j < 32 for the keys this thread holds (element
+// e = tid + r * kCbThreads; the partner e ^ j is in the same warp, so the
+// exchange is a shuffle, not a barrier-separated pass).
+__device__ __forceinline__ uint64_t bitonic_warp_stages(uint64_t x, uint32_t e, uint32_t k, uint32_t jmax) {
+    for (uint32_t j = jmax; j > 0; j >>= 1) {
+        const uint64_t y = __shfl_xor_sync(0xFFFFFFFFu, x, j);
+        const bool up = (e & k) == 0, lower = (e & j) == 0;
+        x = (lower == up) ? (x < y ? x : y) : (x < y ? y : x);
+    }
+    return x;
+}
+
 // index of the first element > t in sorted w[lo, hi), one warp cooperating
 __device__ uint32_t warp_upper_bound(const uint32_t *w, uint32_t lo, uint32_t hi, uint32_t t) {
     const uint32_t lane = threadIdx.x & 31;
@@ -110,7 +122,7 @@ __device__ __forceinline__ uint32_t count_below(const uint32_t *w, uint32_t lo, 
 
 // Builds the codebook of one histogram with the whole CTA; `arrays` holds the
 // construction's arrays (shared memory for small alphabets).
-__device__ void codebook_body(const CbArgs &g, uint8_t *arrays) {
+__device__ __forceinline__ void codebook_body(const CbArgs &g, uint8_t *arrays) {
     __shared__ uint64_t s_sum, s_tbits;
     __shared__ uint32_t s_m, s_c, s_ih, s_it, s_mL, s_mI, s_rounds, s_maxlen, s_bad;
     __shared__ uint32_t s_count[HUFF_MAX_LEN + 1];
@@ -156,9 +168,12 @@ __device__ void codebook_body(const CbArgs &g, uint8_t *arrays) {
     if (overflow && tid == 0) set_error(g.status, HUFF_ERR_HIST_OVERFLOW);
 
     if (m >= 2) {
-        // ---- bitonic sort of the keys (ascending: count, then id; unused last)
+        // ---- bitonic sort of the keys (ascending: count, then id; unused last).
+        // Passes of stride >= 32 exchange through shared memory with a barrier
+        // each; for every k, all strides below 32 run as warp shuffles in one
+        // pass over the thread's elements.
         for (uint32_t k = 2; k <= P; k <<= 1) {
-            for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+            for (uint32_t j = k >> 1; j >= 32; j >>= 1) {
                 for (uint32_t i = tid; i < P / 2; i += kCbThreads) {
                     uint32_t lo = 2 * i - (i & (j - 1));
                     uint32_t hi = lo + j;
@@ -168,6 +183,20 @@ __device__ void codebook_body(const CbArgs &g, uint8_t *arrays) {
                 }
                 __syncthreads();
             }
+            const uint32_t jmax = (k >> 1) < 16 ? (k >> 1) : 16;
+            if (P >= 32) {
+                for (uint32_t e = tid; e < P; e += kCbThreads)
+                    A.keys[e] = bitonic_warp_stages(A.keys[e], e, k, jmax);
+            } else {
+                // fewer keys than a warp: pad the shuffle partners with the largest key
+                const uint32_t e = tid;
+                if (warp == 0) {
+                    uint64_t x = e < P ? A.keys[e] : ~0ull;
+                    x = bitonic_warp_stages(x, e, k, jmax);
+                    if (e < P) A.keys[e] = x;
+                }
+            }
+            __syncthreads();
         }
         for (uint32_t i = tid; i < m; i += kCbThreads) A.wL[i] = (uint32_t)(A.keys[i] >> 16);
         if (tid == 0) { s_c = 0; s_ih = 0; s_it = 0; s_rounds = 0; }
@@ -323,14 +352,14 @@ __device__ void codebook_body(const CbArgs &g, uint8_t *arrays) {
     }
 }
 
-__global__ void __launch_bounds__(kCbThreads) codebook_kernel(CbArgs g) {
+__global__ void __launch_bounds__(kCbThreads, 1) codebook_kernel(CbArgs g) {
     extern __shared__ __align__(16) uint8_t smem[];
     codebook_body(g, g.nbins <= kCbSmemBins ? smem : g.scratch);
 }
 
 // Codebooks of a batch: CTA b builds those of fields b, b + grid, ...;
 // alphabets above the shared-memory limit use scratch + b * scratch_stride.
-__global__ void __launch_bounds__(kCbThreads) codebook_batch_kernel(const CbArgs *gs, uint32_t nfields,
+__global__ void __launch_bounds__(kCbThreads, 1) codebook_batch_kernel(const CbArgs *gs, uint32_t nfields,
                                                                      uint8_t *scratch, size_t scratch_stride) {
     extern __shared__ __align__(16) uint8_t smem[];
     for (uint32_t f = blockIdx.x; f < nfields; f += gridDim.x) {

@@ -102,6 +102,13 @@ huff_status encode_batch_launch(huff_dtype dtype, const EncField *d_fields, uint
                                 const EncBatchConf *d_conf, uint32_t max_nbins, uint8_t *scratch, uint32_t grid,
                                 cudaStream_t st);
 
+// The paper's three-kernel encode (merge = HUFF_MERGE_SHUFFLE).
+size_t shuffle_scratch_bytes(uint64_t n, int chunk_log2, int reduce_log2);
+huff_status encode_shuffle_launch(const void *d_sym, uint64_t n, huff_dtype dtype, const void *d_codebook,
+                                  uint32_t nbins, int chunk_log2, int reduce_log2, uint32_t max_len, uint32_t *d_out,
+                                  uint64_t cap, uint64_t *d_offs, uint64_t *d_total, uint8_t *scratch,
+                                  uint32_t *status, cudaStream_t st);
+
 // ---------------------------------------------------------------- decode
 
 huff_status decode_launch(const uint32_t *d_in, uint64_t total_bits, const uint64_t *d_offs, int chunk_log2,
