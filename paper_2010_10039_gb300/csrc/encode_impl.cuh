@@ -492,6 +492,25 @@ __device__ __forceinline__ uint32_t merge_vec(const uint32_t *sv, uint32_t valid
     return tot;
 }
 
+// Places a run longer than 64 bits codeword by codeword (symbols from global
+// memory: the stage may be refilled already).  Kept out of line so the rare
+// path adds no registers or instructions to the placement loop.
+template <typename Sym, typename Entry, bool GTAB, uint32_t RMASK>
+__device__ __noinline__ void place_long_run(uint32_t *ring, uint32_t base, uint32_t pos, const Sym *symp,
+                                            uint64_t first, int count, uint64_t n, const Entry *tab,
+                                            const uint64_t *gcw, uint32_t nbins, uint32_t tmask) {
+    BitSink<RMASK> sink;
+    sink.begin(ring, base, pos);
+    for (int x = 0; x < count; x++) {
+        const uint64_t i = first + x;
+        if (i >= n) break;
+        Entry en = table_get<Entry, GTAB>(tab, gcw, (uint32_t)symp[i], nbins, tmask);
+        const uint32_t l = ent_len<Entry>(en);
+        if (l) sink.put64(ent_code<Entry>(en), l);
+    }
+    sink.end();
+}
+
 // Loads the shared-memory codebook of a field: tslots entries, those past
 // nbins without codeword.  Merge threads only.
 template <typename Entry>
@@ -693,19 +712,10 @@ __device__ void merge_warps(const EncArgs &a, const EncField *fields, const uint
                     if (bb <= 64) {
                         if (bb) place_run<RMASK>(ring, base, pos, acc[k][r], bb);
                     } else {
-                        // longer than the register: write codeword by codeword
-                        BitSink<RMASK> sink;
-                        sink.begin(ring, base, pos);
-                        for (int x = 0; x < RL; x++) {
-                            const uint64_t i = s0 + (uint64_t)q * V + r * RL + x;
-                            if (i >= n) break;
-                            // the stage may be refilled already: read the symbol from global memory
-                            const uint32_t sx = (uint32_t)symp[i];
-                            Entry en = table_get<Entry, GTAB>(tab, gcw, sx, nbins, tmask);
-                            const uint32_t l = ent_len<Entry>(en);
-                            if (l) sink.put64(ent_code<Entry>(en), l);
-                        }
-                        sink.end();
+                        // longer than the register (rare): codeword by codeword, out of line
+                        place_long_run<Sym, Entry, GTAB, RMASK>(ring, base, pos, symp,
+                                                               s0 + (uint64_t)q * V + r * RL, RL, n, tab, gcw,
+                                                               nbins, tmask);
                     }
                     pos += bb;
                 }
@@ -804,25 +814,43 @@ __device__ void writeout_loop(const EncField *fields, uint32_t *ring, uint32_t t
         // ring neighbour may already hold the next tile (of another field)
         const uint32_t tail_mask = (last && tail_bits) ? ~0u << (32 - tail_bits) : ~0u;
         bool over = false;
-        // stream word w0 + i holds tile bits [32 i - g31, 32 i - g31 + 32): four
-        // independent words per lane per step, each step four coalesced stores
+        // stream word w0 + i holds tile bits [32 i - g31, 32 i - g31 + 32), i.e.
+        // the funnel shift of ring words wb + i and wb + i + 1 (one SHF, which
+        // also covers sh = 0).  A block of 128 words that is whole, inside the
+        // capacity, does not hold the shared first word and does not hold a
+        // masked last word takes no per-word checks (the test is warp-uniform).
+        // Four independent words per lane per step, four coalesced stores.
         const uint32_t sh = (32 - g31) & 31;
-        for (uint32_t i0 = 0; i0 < nw; i0 += 128) {
+        const uint32_t wb = base - (g31 ? 1u : 0u);
+        uint32_t *outw = out + w0;
+        const uint64_t room = cap > w0 ? cap - w0 : 0;                // words writable from w0
+        for (uint32_t b0 = 0; b0 < nw; b0 += 128) {
+            const bool fast = b0 + 128 <= nw && (uint64_t)(b0 + 128) <= room && !(b0 == 0 && g31) &&
+                              !(b0 + 128 == nw && last && tail_bits);
             uint32_t val[4];
+            if (fast) {
 #pragma unroll
-            for (int k = 0; k < 4; k++) {
-                const uint32_t i = i0 + 32 * k + lane;
-                const uint32_t w = base + i - (g31 ? 1 : 0);    // ring word holding the word's first bit
-                const uint32_t hi = ring[w & RMASK], lo = ring[(w + 1) & RMASK];
-                val[k] = sh ? (hi << sh) | (lo >> (32 - sh)) : hi;
-                if (i == 0 && g31) val[k] = ((prev & ((1u << g31) - 1)) << (32 - g31)) | (lo >> g31);
-                if (i == nw - 1) val[k] &= tail_mask;
-            }
+                for (int k = 0; k < 4; k++) {
+                    const uint32_t i = b0 + 32 * k + lane;
+                    val[k] = __funnelshift_l(ring[(wb + i + 1) & RMASK], ring[(wb + i) & RMASK], sh);
+                }
 #pragma unroll
-            for (int k = 0; k < 4; k++) {
-                const uint32_t i = i0 + 32 * k + lane;
-                if (i < nw) {
-                    if (w0 + i < cap) out[w0 + i] = val[k]; else over = true;
+                for (int k = 0; k < 4; k++) outw[b0 + 32 * k + lane] = val[k];
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const uint32_t i = b0 + 32 * k + lane;
+                    const uint32_t hi = ring[(wb + i) & RMASK], lo = ring[(wb + i + 1) & RMASK];
+                    val[k] = __funnelshift_l(lo, hi, sh);
+                    if (i == 0 && g31) val[k] = ((prev & ((1u << g31) - 1)) << (32 - g31)) | (lo >> g31);
+                    if (i == nw - 1) val[k] &= tail_mask;
+                }
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const uint32_t i = b0 + 32 * k + lane;
+                    if (i < nw) {
+                        if ((uint64_t)i < room) outw[i] = val[k]; else over = true;
+                    }
                 }
             }
         }
