@@ -93,7 +93,9 @@ typedef struct {
     int32_t chunk_log2;    /* M: one chunk offset per 2^M symbols; 4..30; paper default 10     */
     int32_t reduce_log2;   /* r: 2^r consecutive symbols merged per thread in registers;
                               -1 = pick r from the average codeword length (Sec. IV-C rule)   */
-    int32_t block_threads; /* threads per CTA: 128, 256 or 512; 0 = default                   */
+    int32_t block_threads; /* reserved: the encoders' CTA shapes are fixed per dtype (the
+                              autotuner of the batched form picks CTAs per SM); any value is
+                              accepted and ignored                                            */
     int32_t merge;         /* HUFF_MERGE_*                                                    */
 } huff_params;
 
