@@ -201,3 +201,28 @@ def test_batch_launch_count_per_run():
     plan.encode()
     torch.cuda.synchronize()
     assert huff.huff_launch_count() - c0 == k
+
+
+@pytest.mark.slow
+def test_batch_full_size_workload_sampled_against_oracle():
+    """The 512-field workload at full size (1.5 G u16 symbols, drawn on the
+    device), tuned plan as the benchmark runs it; fields across the size
+    range are checked against the oracle (regenerated on the host)."""
+    import paper_2010_10039_gb300 as huff
+    import torch
+    prm = [synth.batch_field_params(j) for j in range(512)]
+    fields = []
+    for j, (n, b) in enumerate(prm):
+        sym = synth.draw_device(4, j, n, synth.cdf_table(synth.laplace_pmf(1024, 512, b)), 2)
+        fields.append({"sym": sym, "nbins": 1024, "chunk_log2": 10,
+                       "out": torch.empty((n * 12 + 31) // 32 + 1, dtype=torch.int32, device="cuda"),
+                       "offsets": torch.empty((n >> 10) + 2, dtype=torch.int64, device="cuda"),
+                       "total_bits": torch.zeros(1, dtype=torch.int64, device="cuda")})
+    plan = huff.BatchPlan(fields, autotune=True)
+    plan.encode()
+    torch.cuda.synchronize()
+    assert plan.status() == [0] * 512
+    order = sorted(range(512), key=lambda j: prm[j][0])
+    for j in (order[0], order[1], order[256], order[400], 7):
+        _check_field(plan, j, fields[j], synth.batch_field(j), 1024)
+    plan.close()

@@ -161,3 +161,39 @@ def test_serve_destroy_with_pending_jobs():
     a, nb = jobs[0]
     r = Run(a, nb).all()
     assert r.status() == 0
+
+
+@pytest.mark.slow
+def test_serve_full_size_requests_sampled_against_oracle():
+    """Requests of the served workload at full size (n up to 67 M; u8 Zipf
+    and u16 Gaussian/Laplace), drawn on the device and submitted together;
+    the small ones are re-encoded by the oracle, every job equals its plain
+    single call."""
+    import paper_2010_10039_gb300 as huff
+    import torch
+    reqs = [synth.served_request(i) for i in range(48)]
+    dev = [synth.draw_device(5, 100 + i, n, table, w) for i, (w, n, nb, table) in enumerate(reqs)]
+    srv = huff.Server(mem_budget_bytes=8 << 30, nstreams=4, max_batch=64)
+    try:
+        tickets = [srv.submit(d, r[2]) for d, r in zip(dev, reqs)]
+        res = [srv.wait(t) for t in tickets]
+        assert all(r["status"] == 0 for r in res)
+        small = [i for i, r in enumerate(reqs) if r[1] <= (1 << 21)][:4]
+        assert small
+        for i in small:
+            a = synth.served_symbols(i)
+            nb = reqs[i][2]
+            words, offs, book, tb = _result_arrays(huff, res[i], a.size, nb)
+            want = oracle.codebook(oracle.histogram(a, nb))
+            w, o, otb = oracle.encode(a, want, chunk_log2=10)
+            assert tb == otb and np.array_equal(words, w) and np.array_equal(offs, o)
+        for i in (0, 1, 2, int(np.argmax([r[1] for r in reqs]))):
+            run = Run(dev[i].cpu().numpy().view({1: np.uint8, 2: np.uint16}[reqs[i][0]]), reqs[i][2]).all()
+            assert run.status() == 0
+            gw, gtb = run.stream_np()
+            words, offs, book, tb = _result_arrays(huff, res[i], reqs[i][1], reqs[i][2])
+            assert tb == gtb and np.array_equal(words, gw) and np.array_equal(offs, run.offs_np())
+        for t in tickets:
+            srv.release(t)
+    finally:
+        srv.close()
