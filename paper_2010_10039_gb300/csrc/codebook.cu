@@ -17,14 +17,15 @@
 // serial order (equal-weight leaves win the tie, equal-weight joined nodes
 // are older), and the pairs leave two by two, so the serial construction melds
 // exactly these pairs; an odd k leaves S[k-1] to pair with S0+S1 next round.
-// The paper's sync-separated parallel regions become __syncthreads() of one
-// 1024-thread CTA; the merge ranks each node by binary search in the other
-// queue (the stable form of Merge Path's co-ranking).
+// The paper's sync-separated parallel regions become one 1024-thread CTA with
+// a single barrier per round: every warp derives the round's t and node counts
+// itself (the same reads give the same result), and thread j melds pair j
+// after finding S[2j] by a Merge Path co-ranking search in the two queues, so
+// the merged order is never materialised.
 //
 // Lengths.  Instead of walking every leaf to its leader each round
-// (UpdateLeafNode), each meld records the parent of its two inputs; one pass
-// over the rounds in reverse gives every joined node its depth, and a leaf's
-// length is its parent's depth plus one.
+// (UpdateLeafNode), each meld records the parent of its two inputs; after the
+// last round a leaf's length is the number of parent links from it to the root.
 //
 // GenerateCW + canonisation (Sec. IV-B2).  Code lengths are counted per
 // length; First is filled from the longest length down so that a shorter
@@ -40,13 +41,11 @@ constexpr int kCbThreads = 1024;
 constexpr uint32_t kCbSmemBins = 4096;     // arrays live in shared memory up to this alphabet
 
 struct CbArrays {
-    uint64_t *keys;     // P       sort keys (count << 16 | id), unused = ~0
+    uint64_t *keys;     // 2P      sort keys (count << 16 | id), unused = ~0; the second
+                        //         half is the exchange buffer of the register sort
     uint32_t *wL;       // m       leaf weights (sorted)
     uint32_t *wI;       // m       joined-node weights (creation order)
-    uint32_t *parent;   // 2m      parent node id of every node
-    uint32_t *temp;     // m       merged order of this round (node ids)
-    uint32_t *rstart;   // m       first joined node of each round
-    uint32_t *depthI;   // m       depth of joined nodes
+    uint32_t *parent;   // 2m      parent node id of every node (leaves 0..m-1, joined m..2m-2)
     uint8_t *lenS;      // nbins   length by symbol id
 };
 
@@ -60,19 +59,16 @@ __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(
 
 __host__ __device__ inline size_t cb_array_bytes(uint32_t nbins) {
     size_t P = pow2_ceil(nbins);
-    return align16(P * 8) + 6 * align16((size_t)nbins * 4) + align16((size_t)nbins * 8) + align16(nbins);
+    return align16(P * 16) + 2 * align16((size_t)nbins * 4) + align16((size_t)nbins * 8) + align16(nbins);
 }
 
 __device__ inline CbArrays cb_carve(uint8_t *p, uint32_t nbins) {
     CbArrays a;
     size_t P = pow2_ceil(nbins);
-    a.keys = reinterpret_cast<uint64_t *>(p); p += align16(P * 8);
+    a.keys = reinterpret_cast<uint64_t *>(p); p += align16(P * 16);
     a.wL = reinterpret_cast<uint32_t *>(p); p += align16((size_t)nbins * 4);
     a.wI = reinterpret_cast<uint32_t *>(p); p += align16((size_t)nbins * 4);
     a.parent = reinterpret_cast<uint32_t *>(p); p += align16((size_t)nbins * 8);
-    a.temp = reinterpret_cast<uint32_t *>(p); p += align16((size_t)nbins * 4);
-    a.rstart = reinterpret_cast<uint32_t *>(p); p += align16((size_t)nbins * 4);
-    a.depthI = reinterpret_cast<uint32_t *>(p); p += align16((size_t)nbins * 4);
     a.lenS = p;
     return a;
 }
@@ -87,6 +83,63 @@ __device__ __forceinline__ uint64_t bitonic_warp_stages(uint64_t x, uint32_t e, 
         x = (lower == up) ? (x < y ? x : y) : (x < y ? y : x);
     }
     return x;
+}
+
+// Ascending bitonic sort of P <= kCbThreads keys, thread e holding element e
+// (threads e >= P hold ~0 and are never read).  Strides of 32 and more go
+// through shared memory, alternating between buf[0, P) and buf[P, 2P) so that
+// one barrier per stride suffices; smaller strides are shuffles.
+__device__ __forceinline__ uint64_t bitonic_sort_regs(uint64_t x, uint32_t P, uint64_t *buf) {
+    const uint32_t e = threadIdx.x;
+    uint32_t flip = 0;
+    for (uint32_t k = 2; k <= P; k <<= 1) {
+        for (uint32_t j = k >> 1; j >= 32; j >>= 1) {
+            uint64_t *b = buf + flip * P;
+            flip ^= 1;
+            if (e < P) b[e] = x;
+            __syncthreads();
+            if (e < P) {
+                const uint64_t y = b[e ^ j];
+                const bool up = (e & k) == 0, lower = (e & j) == 0;
+                x = (lower == up) ? (x < y ? x : y) : (x < y ? y : x);
+            }
+        }
+        // within a warp: lanes below P pair only with lanes below P
+        x = bitonic_warp_stages(x, e, k, (k >> 1) < 16 ? (k >> 1) : 16);
+    }
+    return x;
+}
+
+// Upper bounds of t in the sorted ranges wa[alo, ahi) and wb[blo, bhi) (index
+// of the first element > t), one warp searching both side by side so that
+// their loads overlap.
+__device__ __forceinline__ void warp_upper_bound2(const uint32_t *wa, uint32_t alo, uint32_t ahi,
+                                                  const uint32_t *wb, uint32_t blo, uint32_t bhi, uint32_t t,
+                                                  uint32_t &ra, uint32_t &rb) {
+    const uint32_t lane = threadIdx.x & 31;
+    bool adone = false, bdone = false;
+    while (true) {
+        const bool awide = !adone && ahi - alo > 32, bwide = !bdone && bhi - blo > 32;
+        if (!awide && !bwide) break;
+        const uint32_t as = (ahi - alo + 31) / 32, bs = (bhi - blo + 31) / 32;
+        const uint32_t ap = alo + lane * as, bp = blo + lane * bs;
+        const bool pa = awide && ap < ahi && wa[ap] <= t;
+        const bool pb = bwide && bp < bhi && wb[bp] <= t;
+        const uint32_t ca = __popc(__ballot_sync(0xFFFFFFFFu, pa));
+        const uint32_t cb = __popc(__ballot_sync(0xFFFFFFFFu, pb));
+        if (awide) {
+            if (ca == 0) { ahi = alo; adone = true; }
+            else { const uint32_t nhi = alo + ca * as; alo = alo + (ca - 1) * as + 1; ahi = nhi < ahi ? nhi : ahi; }
+        }
+        if (bwide) {
+            if (cb == 0) { bhi = blo; bdone = true; }
+            else { const uint32_t nhi = blo + cb * bs; blo = blo + (cb - 1) * bs + 1; bhi = nhi < bhi ? nhi : bhi; }
+        }
+    }
+    const bool pa = alo + lane < ahi && wa[alo + lane] <= t;
+    const bool pb = blo + lane < bhi && wb[blo + lane] <= t;
+    ra = alo + __popc(__ballot_sync(0xFFFFFFFFu, pa));
+    rb = blo + __popc(__ballot_sync(0xFFFFFFFFu, pb));
 }
 
 // index of the first element > t in sorted w[lo, hi), one warp cooperating
@@ -108,23 +161,11 @@ __device__ uint32_t warp_upper_bound(const uint32_t *w, uint32_t lo, uint32_t hi
     return lo + __popc(__ballot_sync(0xFFFFFFFFu, pred));
 }
 
-// number of elements in sorted w[lo, hi) that are < t (strict) or <= t
-template <bool STRICT>
-__device__ __forceinline__ uint32_t count_below(const uint32_t *w, uint32_t lo, uint32_t hi, uint32_t t) {
-    uint32_t a = lo, b = hi;
-    while (a < b) {
-        uint32_t mid = (a + b) >> 1;
-        bool go = STRICT ? (w[mid] < t) : (w[mid] <= t);
-        if (go) a = mid + 1; else b = mid;
-    }
-    return a - lo;
-}
-
 // Builds the codebook of one histogram with the whole CTA; `arrays` holds the
 // construction's arrays (shared memory for small alphabets).
 __device__ __forceinline__ void codebook_body(const CbArgs &g, uint8_t *arrays) {
     __shared__ uint64_t s_sum, s_tbits;
-    __shared__ uint32_t s_m, s_c, s_ih, s_it, s_mL, s_mI, s_rounds, s_maxlen, s_bad;
+    __shared__ uint32_t s_m, s_maxlen, s_bad;
     __shared__ uint32_t s_count[HUFF_MAX_LEN + 1];
     __shared__ uint32_t s_base[HUFF_MAX_LEN + 1];
     __shared__ uint64_t s_first[HUFF_MAX_LEN + 1];
@@ -134,6 +175,7 @@ __device__ __forceinline__ void codebook_body(const CbArgs &g, uint8_t *arrays) 
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t nbins = g.nbins;
     const uint32_t P = pow2_ceil(nbins);
+    const bool small = P <= kCbThreads;      // one bin per thread: keys stay in registers
     CbArrays A = cb_carve(arrays, nbins);
     huff_codebook_header *hdr = reinterpret_cast<huff_codebook_header *>(g.book);
     uint64_t *cw = reinterpret_cast<uint64_t *>(g.book + cb_cw_offset());
@@ -141,11 +183,12 @@ __device__ __forceinline__ void codebook_body(const CbArgs &g, uint8_t *arrays) 
 
     if (tid == 0) { s_sum = 0; s_tbits = 0; s_m = 0; s_bad = 0; s_maxlen = 0; }
     if (tid <= HUFF_MAX_LEN) { s_count[tid] = 0; s_base[tid] = 0; s_first[tid] = 0; s_entry[tid] = 0; }
+    for (uint32_t i = tid; i < (kCbThreads / 32) * (HUFF_MAX_LEN + 1); i += kCbThreads) (&s_wcnt[0][0])[i] = 0;
     __syncthreads();
 
     // ---- keys, used count, histogram sum
-    uint64_t part = 0;
-    uint32_t used = 0;
+    uint64_t part = 0, mykey = ~0ull;
+    uint32_t used = 0, mycount = 0;
     for (uint32_t i = tid; i < P; i += kCbThreads) {
         uint64_t key = ~0ull;
         if (i < nbins) {
@@ -154,8 +197,10 @@ __device__ __forceinline__ void codebook_body(const CbArgs &g, uint8_t *arrays) 
             if (c) { key = ((uint64_t)c << 16) | i; used++; }
             A.lenS[i] = 0;
             cw[i] = 0;
+            mycount = c;
         }
-        A.keys[i] = key;
+        if (small) mykey = key;
+        else A.keys[i] = key;
     }
     for (int o = 16; o; o >>= 1) {
         part += __shfl_xor_sync(0xFFFFFFFFu, part, o);
@@ -168,107 +213,101 @@ __device__ __forceinline__ void codebook_body(const CbArgs &g, uint8_t *arrays) 
     if (overflow && tid == 0) set_error(g.status, HUFF_ERR_HIST_OVERFLOW);
 
     if (m >= 2) {
-        // ---- bitonic sort of the keys (ascending: count, then id; unused last).
-        // Passes of stride >= 32 exchange through shared memory with a barrier
-        // each; for every k, all strides below 32 run as warp shuffles in one
-        // pass over the thread's elements.
-        for (uint32_t k = 2; k <= P; k <<= 1) {
-            for (uint32_t j = k >> 1; j >= 32; j >>= 1) {
-                for (uint32_t i = tid; i < P / 2; i += kCbThreads) {
-                    uint32_t lo = 2 * i - (i & (j - 1));
-                    uint32_t hi = lo + j;
-                    uint64_t x = A.keys[lo], y = A.keys[hi];
-                    bool up = (lo & k) == 0;
-                    if ((x > y) == up) { A.keys[lo] = y; A.keys[hi] = x; }
+        // ---- bitonic sort of the keys (ascending: count, then id; unused last)
+        if (small) {
+            // the exchange buffers are keys[0, 2P): every thread must be done
+            // reading them before the sorted keys go back to keys[0, P)
+            mykey = bitonic_sort_regs(mykey, P, A.keys);
+            __syncthreads();
+            if (tid < P) A.keys[tid] = mykey;
+        } else {
+            // passes of stride >= 32 exchange through shared memory with a
+            // barrier each; for every k, all strides below 32 run as warp
+            // shuffles in one pass over the thread's elements
+            for (uint32_t k = 2; k <= P; k <<= 1) {
+                for (uint32_t j = k >> 1; j >= 32; j >>= 1) {
+                    for (uint32_t i = tid; i < P / 2; i += kCbThreads) {
+                        uint32_t lo = 2 * i - (i & (j - 1));
+                        uint32_t hi = lo + j;
+                        uint64_t x = A.keys[lo], y = A.keys[hi];
+                        bool up = (lo & k) == 0;
+                        if ((x > y) == up) { A.keys[lo] = y; A.keys[hi] = x; }
+                    }
+                    __syncthreads();
                 }
-                __syncthreads();
-            }
-            const uint32_t jmax = (k >> 1) < 16 ? (k >> 1) : 16;
-            if (P >= 32) {
+                const uint32_t jmax = (k >> 1) < 16 ? (k >> 1) : 16;
                 for (uint32_t e = tid; e < P; e += kCbThreads)
                     A.keys[e] = bitonic_warp_stages(A.keys[e], e, k, jmax);
-            } else {
-                // fewer keys than a warp: pad the shuffle partners with the largest key
-                const uint32_t e = tid;
-                if (warp == 0) {
-                    uint64_t x = e < P ? A.keys[e] : ~0ull;
-                    x = bitonic_warp_stages(x, e, k, jmax);
-                    if (e < P) A.keys[e] = x;
-                }
+                __syncthreads();
             }
-            __syncthreads();
         }
+        __syncthreads();
         for (uint32_t i = tid; i < m; i += kCbThreads) A.wL[i] = (uint32_t)(A.keys[i] >> 16);
-        if (tid == 0) { s_c = 0; s_ih = 0; s_it = 0; s_rounds = 0; }
         __syncthreads();
 
-        // ---- GenerateCL rounds
-        for (;;) {
-            const uint32_t c = s_c, ih = s_ih, it = s_it;
-            if ((m - c) + (it - ih) < 2) break;
-            if (warp == 0) {
-                // the two lightest nodes, leaf first on equal weight
-                uint32_t pc = c, pi = ih;
-                uint64_t t = 0;
-                for (int q = 0; q < 2; q++) {
-                    bool leaf = pc < m && (pi >= it || A.wL[pc] <= A.wI[pi]);
-                    t += leaf ? A.wL[pc++] : A.wI[pi++];
-                }
-                const uint32_t tt = (uint32_t)t;   // the total is < 2^32
-                uint32_t kL = warp_upper_bound(A.wL, c, m, tt) - c;
-                uint32_t kI = warp_upper_bound(A.wI, ih, it, tt) - ih;
-                if ((kL + kI) & 1) {
+        // ---- GenerateCL rounds.  c leaves and the joined nodes before ih have
+        // been melded; joined nodes ih..it-1 wait.  The first rt threads run the
+        // rounds (every warp repeats the selection, so fewer warps repeat less
+        // of it; larger alphabets have more pairs per round and get more) and
+        // all track the same (c, ih, it).  Within a round the reads (wL,
+        // wI[ih, it)) and the writes (wI[it, it + pairs), parent) never
+        // overlap, so one named barrier per round suffices.
+        const uint32_t rt = m <= 2048 ? 256u : (m <= 16384 ? 512u : (uint32_t)kCbThreads);
+        if (tid < rt) {
+            constexpr uint64_t kNone = 1ull << 33;     // above every weight (totals are < 2^32)
+            uint32_t c = 0, ih = 0, it = 0;
+            while ((m - c) + (it - ih) >= 2) {
+                // t: the two lightest nodes, a leaf first on equal weight
+                const uint64_t a0 = c < m ? A.wL[c] : kNone, a1 = c + 1 < m ? A.wL[c + 1] : kNone;
+                const uint64_t b0 = ih < it ? A.wI[ih] : kNone, b1 = ih + 1 < it ? A.wI[ih + 1] : kNone;
+                const uint64_t t = a0 <= b0 ? a0 + (a1 <= b0 ? a1 : b0) : b0 + (a0 <= b1 ? a0 : b1);
+                uint32_t mL, mI;
+                warp_upper_bound2(A.wL, c, m, A.wI, ih, it, (uint32_t)t, mL, mI);
+                mL -= c;
+                mI -= ih;
+                if ((mL + mI) & 1) {
                     // drop the last node of the merged order: a joined node wins ties for last
-                    bool dropI = kI > 0 && (kL == 0 || A.wI[ih + kI - 1] >= A.wL[c + kL - 1]);
-                    if (dropI) kI--; else kL--;
+                    const uint32_t lastI = mI ? A.wI[ih + mI - 1] : 0u, lastL = mL ? A.wL[c + mL - 1] : 0u;
+                    const bool dropI = mI > 0 && (mL == 0 || lastI >= lastL);
+                    if (dropI) mI--; else mL--;
                 }
-                if (lane == 0) { s_mL = kL; s_mI = kI; }
+                const uint32_t pairs = (mL + mI) >> 1;
+                const uint32_t *wa = A.wL + c, *wb = A.wI + ih;
+                for (uint32_t j = tid; j < pairs; j += rt) {
+                    // leaves among the first 2j nodes of the stable leaf-first merge:
+                    // the least i with wa[i] > wb[2j - 1 - i]
+                    const uint32_t p = 2 * j;
+                    uint32_t lo = p > mI ? p - mI : 0, hi = p < mL ? p : mL;
+                    while (lo < hi) {
+                        const uint32_t mid = (lo + hi) >> 1;
+                        if (wa[mid] <= wb[p - 1 - mid]) lo = mid + 1; else hi = mid;
+                    }
+                    uint32_t ia = lo, ib = p - lo, wsum = 0;
+                    uint32_t node[2];
+#pragma unroll
+                    for (int q = 0; q < 2; q++) {
+                        const bool leaf = ia < mL && (ib >= mI || wa[ia] <= wb[ib]);
+                        if (leaf) { node[q] = c + ia; wsum += wa[ia]; ia++; }
+                        else { node[q] = m + ih + ib; wsum += wb[ib]; ib++; }
+                    }
+                    A.wI[it + j] = wsum;
+                    A.parent[node[0]] = m + it + j;
+                    A.parent[node[1]] = m + it + j;
+                }
+                c += mL;
+                ih += mI;
+                it += pairs;
+                asm volatile("bar.sync 1, %0;" ::"r"(rt) : "memory");
             }
-            __syncthreads();
-            const uint32_t mL = s_mL, mI = s_mI;
-            // stable leaf-first merge by ranking each node in the other queue
-            for (uint32_t a = tid; a < mL; a += kCbThreads) {
-                uint32_t r = a + count_below<true>(A.wI, ih, ih + mI, A.wL[c + a]);
-                A.temp[r] = c + a;
-            }
-            for (uint32_t b = tid; b < mI; b += kCbThreads) {
-                uint32_t r = b + count_below<false>(A.wL, c, c + mL, A.wI[ih + b]);
-                A.temp[r] = m + ih + b;
-            }
-            __syncthreads();
-            const uint32_t pairs = (mL + mI) >> 1;
-            for (uint32_t j = tid; j < pairs; j += kCbThreads) {
-                uint32_t x = A.temp[2 * j], y = A.temp[2 * j + 1];
-                uint32_t wx = x < m ? A.wL[x] : A.wI[x - m];
-                uint32_t wy = y < m ? A.wL[y] : A.wI[y - m];
-                A.wI[it + j] = wx + wy;
-                A.parent[x] = m + it + j;
-                A.parent[y] = m + it + j;
-            }
-            if (tid == 0) {
-                A.rstart[s_rounds] = it;
-                s_rounds++;
-                s_c = c + mL;
-                s_ih = ih + mI;
-                s_it = it + pairs;
-            }
-            __syncthreads();
         }
-
-        // ---- depths: rounds in reverse (a parent is always made in a later round)
-        const uint32_t nI = m - 1, rounds = s_rounds;
-        if (tid == 0) A.depthI[nI - 1] = 0;
         __syncthreads();
-        for (int r = (int)rounds - 1; r >= 0; r--) {
-            uint32_t j0 = A.rstart[r];
-            uint32_t j1 = (r + 1 < (int)rounds) ? A.rstart[r + 1] : nI;
-            for (uint32_t j = j0 + tid; j < j1; j += kCbThreads)
-                if (j != nI - 1) A.depthI[j] = A.depthI[A.parent[m + j] - m] + 1;
-            __syncthreads();
-        }
+
+        // ---- lengths: parent links from each leaf to the root (joined node m - 2)
+        const uint32_t root = 2 * m - 2;
         uint32_t bad = 0;
         for (uint32_t v = tid; v < m; v += kCbThreads) {
-            uint32_t d = A.depthI[A.parent[v] - m] + 1;
+            uint32_t d = 0, x = v;
+            while (x != root && d <= HUFF_MAX_LEN) { x = A.parent[x]; d++; }
             if (d > HUFF_MAX_LEN) { bad = 1; d = HUFF_MAX_LEN; }
             A.lenS[(uint32_t)(A.keys[v] & 0xFFFF)] = (uint8_t)d;
         }
@@ -284,57 +323,90 @@ __device__ __forceinline__ void codebook_body(const CbArgs &g, uint8_t *arrays) 
         __syncthreads();
     }
 
-    // ---- canonical codewords, First, Entry, reverse codebook
+    // ---- canonical codewords, First, Entry, reverse codebook.  Ids are taken
+    // in slices of kCbThreads; within a slice, a warp match gives each id its
+    // rank among the warp's ids of equal length, and a per-length scan over
+    // the warps (one warp per length) its rank in the slice.
+    uint32_t l_mine = 0, rank_w = 0;
+    auto slice_ranks = [&](uint32_t base) {
+        const uint32_t id = base + tid;
+        l_mine = id < nbins ? A.lenS[id] : 0;
+        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, l_mine);
+        rank_w = __popc(peers & ((1u << lane) - 1));
+        if (rank_w == 0) s_wcnt[warp][l_mine] = __popc(peers);
+        __syncthreads();
+        for (uint32_t l = warp + 1; l <= HUFF_MAX_LEN; l += kCbThreads / 32) {
+            const uint32_t b = s_base[l], cnt = s_wcnt[lane][l];
+            uint32_t inc = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            s_wcnt[lane][l] = b + inc - cnt;
+            __syncwarp();
+            if (lane == 31) s_base[l] = b + inc;
+        }
+        __syncthreads();
+    };
+    auto first_entry = [&]() {
+        // First from the longest length down; Entry as the running count
+        if (tid == 0) {
+            uint32_t maxl = 0;
+            for (uint32_t l = 1; l <= HUFF_MAX_LEN; l++) if (s_count[l]) maxl = l;
+            s_maxlen = maxl;
+            uint64_t f = 0;
+            for (int l = (int)maxl - 1; l >= 1; l--) {
+                f = (f + s_count[l + 1] + 1) >> 1;
+                s_first[l] = f;
+            }
+            uint32_t e = 0;
+            for (uint32_t l = 1; l < HUFF_MAX_LEN; l++) {
+                e += s_count[l];
+                s_entry[l + 1] = e;
+            }
+        }
+        __syncthreads();
+    };
+    auto write_codes = [&](uint32_t base) {
+        const uint32_t id = base + tid;
+        if (l_mine) {
+            const uint32_t rank = s_wcnt[warp][l_mine] + rank_w;
+            cw[id] = (s_first[l_mine] + rank) | ((uint64_t)l_mine << HUFF_CW_LEN_SHIFT);
+            sorted_syms[s_entry[l_mine] + rank] = id;
+        }
+    };
     uint64_t tb = 0;
-    for (uint32_t i = tid; i < nbins; i += kCbThreads) {
-        uint32_t l = A.lenS[i];
-        if (l) {
-            atomicAdd(&s_count[l], 1u);
-            tb += (uint64_t)l * g.hist[i];
+    if (nbins <= kCbThreads) {
+        // one slice: its per-length totals are the counts
+        slice_ranks(0);
+        if (l_mine) tb = (uint64_t)l_mine * mycount;
+        if (tid >= 1 && tid <= HUFF_MAX_LEN) s_count[tid] = s_base[tid];
+        __syncthreads();
+        first_entry();
+        write_codes(0);
+    } else {
+        for (uint32_t i = tid; i < nbins; i += kCbThreads) {
+            uint32_t l = A.lenS[i];
+            if (l) {
+                atomicAdd(&s_count[l], 1u);
+                tb += (uint64_t)l * g.hist[i];
+            }
+        }
+        __syncthreads();
+        first_entry();
+        for (uint32_t base = 0; base < nbins; base += kCbThreads) {
+            slice_ranks(base);
+            write_codes(base);
+            __syncthreads();
+            for (uint32_t i = tid; i < (kCbThreads / 32) * (HUFF_MAX_LEN + 1); i += kCbThreads)
+                (&s_wcnt[0][0])[i] = 0;
+            __syncthreads();
         }
     }
     for (int o = 16; o; o >>= 1) tb += __shfl_xor_sync(0xFFFFFFFFu, tb, o);
     if (lane == 0 && tb) atomicAdd((unsigned long long *)&s_tbits, (unsigned long long)tb);
     __syncthreads();
-    if (tid == 0) {
-        uint32_t maxl = 0;
-        for (uint32_t l = 1; l <= HUFF_MAX_LEN; l++) if (s_count[l]) maxl = l;
-        s_maxlen = maxl;
-        if (maxl) {
-            s_first[maxl] = 0;
-            for (int l = (int)maxl - 1; l >= 1; l--) s_first[l] = (s_first[l + 1] + s_count[l + 1] + 1) >> 1;
-        }
-        s_entry[1] = 0;
-        for (uint32_t l = 1; l < HUFF_MAX_LEN; l++) s_entry[l + 1] = s_entry[l] + s_count[l];
-    }
-    __syncthreads();
-    for (uint32_t base = 0; base < nbins; base += kCbThreads) {
-        for (uint32_t i = tid; i < (kCbThreads / 32) * (HUFF_MAX_LEN + 1); i += kCbThreads)
-            (&s_wcnt[0][0])[i] = 0;
-        __syncthreads();
-        const uint32_t id = base + tid;
-        const uint32_t l = id < nbins ? A.lenS[id] : 0;
-        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, l);
-        const uint32_t rank_w = __popc(peers & ((1u << lane) - 1));
-        if (rank_w == 0) s_wcnt[warp][l] = __popc(peers);
-        __syncthreads();
-        if (tid >= 1 && tid <= HUFF_MAX_LEN) {
-            uint32_t off = s_base[tid];
-            for (int w = 0; w < kCbThreads / 32; w++) {
-                uint32_t c = s_wcnt[w][tid];
-                s_wcnt[w][tid] = off;
-                off += c;
-            }
-            s_base[tid] = off;
-        }
-        __syncthreads();
-        if (l) {
-            uint32_t rank = s_wcnt[warp][l] + rank_w;
-            cw[id] = (s_first[l] + rank) | ((uint64_t)l << HUFF_CW_LEN_SHIFT);
-            sorted_syms[s_entry[l] + rank] = id;
-        }
-        __syncthreads();
-    }
     if (tid == 0) {
         hdr->nbins = nbins;
         hdr->max_len = s_maxlen;
