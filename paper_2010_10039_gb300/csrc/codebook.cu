@@ -39,13 +39,17 @@ namespace huff {
 
 constexpr int kCbThreads = 1024;
 constexpr uint32_t kCbSmemBins = 4096;     // arrays live in shared memory up to this alphabet
+constexpr uint32_t kCbRevDepth = 16384;    // above this many used symbols, depths by a per-round pass
+constexpr uint32_t kRadixDigits = 256;     // 8-bit digits of the large-alphabet sort
 
 struct CbArrays {
-    uint64_t *keys;     // 2P      sort keys (count << 16 | id), unused = ~0; the second
-                        //         half is the exchange buffer of the register sort
+    uint64_t *keys;     // 2P      sort keys (count << 16 | id); the two halves are the
+                        //         exchange buffers of the sorts
     uint32_t *wL;       // m       leaf weights (sorted)
     uint32_t *wI;       // m       joined-node weights (creation order)
     uint32_t *parent;   // 2m      parent node id of every node (leaves 0..m-1, joined m..2m-2)
+    uint32_t *rstart;   // m       first joined node of each round     } alphabets above
+    uint32_t *depthI;   // m       depth of each joined node           } kCbSmemBins only
     uint8_t *lenS;      // nbins   length by symbol id
 };
 
@@ -59,7 +63,8 @@ __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(
 
 __host__ __device__ inline size_t cb_array_bytes(uint32_t nbins) {
     size_t P = pow2_ceil(nbins);
-    return align16(P * 16) + 2 * align16((size_t)nbins * 4) + align16((size_t)nbins * 8) + align16(nbins);
+    const size_t rev = nbins > kCbSmemBins ? 2 * align16((size_t)nbins * 4) : 0;
+    return align16(P * 16) + 2 * align16((size_t)nbins * 4) + align16((size_t)nbins * 8) + rev + align16(nbins);
 }
 
 __device__ inline CbArrays cb_carve(uint8_t *p, uint32_t nbins) {
@@ -69,6 +74,11 @@ __device__ inline CbArrays cb_carve(uint8_t *p, uint32_t nbins) {
     a.wL = reinterpret_cast<uint32_t *>(p); p += align16((size_t)nbins * 4);
     a.wI = reinterpret_cast<uint32_t *>(p); p += align16((size_t)nbins * 4);
     a.parent = reinterpret_cast<uint32_t *>(p); p += align16((size_t)nbins * 8);
+    a.rstart = a.depthI = nullptr;
+    if (nbins > kCbSmemBins) {
+        a.rstart = reinterpret_cast<uint32_t *>(p); p += align16((size_t)nbins * 4);
+        a.depthI = reinterpret_cast<uint32_t *>(p); p += align16((size_t)nbins * 4);
+    }
     a.lenS = p;
     return a;
 }
@@ -108,6 +118,90 @@ __device__ __forceinline__ uint64_t bitonic_sort_regs(uint64_t x, uint32_t P, ui
         x = bitonic_warp_stages(x, e, k, (k >> 1) < 16 ? (k >> 1) : 16);
     }
     return x;
+}
+
+// Stable LSD radix sort, by count, of the used bins of hist[nbins] into
+// buf[0, m) as keys count << 16 | id.  Bins enter in id order, so equal counts
+// stay in id order and the result is the (count, id) order.  8-bit digits,
+// as many passes as maxcount has digits; pass 0 reads the histogram and drops
+// unused bins, and the passes alternate between buf[0, P) and buf[P, 2P) so
+// that the last one lands in buf[0, P).  Warp w owns a contiguous segment of
+// each pass's input; its per-digit counts (rh[digit][w]), scanned in
+// digit-major order, give its first slot for each digit, and the lanes of one
+// step rank among themselves by a warp match.  Every count and slot is below
+// 65,536, so they are held as u16.
+__device__ void radix_sort_keys(const uint32_t *hist, uint32_t nbins, uint32_t m, uint32_t maxcount, uint64_t *buf,
+                                uint32_t P, uint16_t (*rh)[32], uint32_t *wsum) {
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t lt = (1u << lane) - 1;
+    const uint32_t bits = 32 - __clz(maxcount);
+    const uint32_t npass = bits > 8 ? (bits + 7) / 8 : 1;
+    for (uint32_t pass = 0; pass < npass; pass++) {
+        const uint32_t shift = 16 + 8 * pass;
+        const uint64_t *src = buf + ((npass - pass) & 1) * P;
+        uint64_t *dst = buf + ((npass - 1 - pass) & 1) * P;
+        const uint32_t len = pass == 0 ? nbins : m;
+        const uint32_t seg = (((len + 31) / 32) + 31) & ~31u;
+        const uint32_t begin = warp * seg < len ? warp * seg : len;
+        const uint32_t end = begin + seg < len ? begin + seg : len;
+        for (uint32_t i = tid; i < kRadixDigits * 32; i += kCbThreads) (&rh[0][0])[i] = 0;
+        __syncthreads();
+        // one step: four loads in flight, then the four groups of 32 in order
+        auto step = [&](uint32_t b, bool scatter) {
+            uint64_t key[4];
+            bool valid[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const uint32_t i = b + 32 * q + lane;
+                valid[q] = i < end;
+                if (pass == 0) {
+                    const uint32_t c = valid[q] ? hist[i] : 0u;
+                    valid[q] = c != 0;
+                    key[q] = ((uint64_t)c << 16) | i;
+                } else {
+                    key[q] = valid[q] ? src[i] : 0ull;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const uint32_t digit = valid[q] ? (uint32_t)(key[q] >> shift) & (kRadixDigits - 1) : 0x10000u;
+                const uint32_t peers = __match_any_sync(0xFFFFFFFFu, digit);
+                const uint32_t rank = __popc(peers & lt);
+                if (!scatter) {
+                    if (valid[q] && rank == 0) rh[digit][warp] += (uint16_t)__popc(peers);
+                } else {
+                    const uint32_t slot = valid[q] ? rh[digit][warp] : 0u;
+                    __syncwarp();
+                    if (valid[q] && rank == 0) rh[digit][warp] = (uint16_t)(slot + __popc(peers));
+                    __syncwarp();
+                    if (valid[q]) dst[slot + rank] = key[q];
+                }
+            }
+        };
+        for (uint32_t b = begin; b < end; b += 128) step(b, false);
+        __syncthreads();
+        // exclusive scan of rh in digit-major order: eight entries per thread
+        uint16_t *flat = &rh[0][0];
+        uint32_t v[8], sum = 0;
+#pragma unroll
+        for (int q = 0; q < 8; q++) { v[q] = flat[8 * tid + q]; sum += v[q]; }
+        uint32_t inc = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) wsum[warp] = inc;
+        __syncthreads();
+        uint32_t wbase = 0;
+        for (uint32_t w = 0; w < warp; w++) wbase += wsum[w];
+        uint32_t run = wbase + inc - sum;
+#pragma unroll
+        for (int q = 0; q < 8; q++) { flat[8 * tid + q] = (uint16_t)run; run += v[q]; }
+        __syncthreads();
+        for (uint32_t b = begin; b < end; b += 128) step(b, true);
+        __syncthreads();
+    }
 }
 
 // Upper bounds of t in the sorted ranges wa[alo, ahi) and wb[blo, bhi) (index
@@ -165,7 +259,9 @@ __device__ uint32_t warp_upper_bound(const uint32_t *w, uint32_t lo, uint32_t hi
 // construction's arrays (shared memory for small alphabets).
 __device__ __forceinline__ void codebook_body(const CbArgs &g, uint8_t *arrays) {
     __shared__ uint64_t s_sum, s_tbits;
-    __shared__ uint32_t s_m, s_maxlen, s_bad;
+    __shared__ uint32_t s_m, s_maxlen, s_bad, s_maxc, s_rounds;
+    __shared__ uint32_t s_wsum[kCbThreads / 32];
+    __shared__ uint16_t s_rh[kRadixDigits][32];
     __shared__ uint32_t s_count[HUFF_MAX_LEN + 1];
     __shared__ uint32_t s_base[HUFF_MAX_LEN + 1];
     __shared__ uint64_t s_first[HUFF_MAX_LEN + 1];
@@ -181,32 +277,34 @@ __device__ __forceinline__ void codebook_body(const CbArgs &g, uint8_t *arrays) 
     uint64_t *cw = reinterpret_cast<uint64_t *>(g.book + cb_cw_offset());
     uint32_t *sorted_syms = reinterpret_cast<uint32_t *>(g.book + cb_sorted_offset(nbins));
 
-    if (tid == 0) { s_sum = 0; s_tbits = 0; s_m = 0; s_bad = 0; s_maxlen = 0; }
+    if (tid == 0) { s_sum = 0; s_tbits = 0; s_m = 0; s_bad = 0; s_maxlen = 0; s_maxc = 0; s_rounds = 0; }
     if (tid <= HUFF_MAX_LEN) { s_count[tid] = 0; s_base[tid] = 0; s_first[tid] = 0; s_entry[tid] = 0; }
     for (uint32_t i = tid; i < (kCbThreads / 32) * (HUFF_MAX_LEN + 1); i += kCbThreads) (&s_wcnt[0][0])[i] = 0;
     __syncthreads();
 
-    // ---- keys, used count, histogram sum
+    // ---- keys (one per thread up to kCbThreads bins), used count, largest
+    // count, histogram sum
     uint64_t part = 0, mykey = ~0ull;
-    uint32_t used = 0, mycount = 0;
-    for (uint32_t i = tid; i < P; i += kCbThreads) {
-        uint64_t key = ~0ull;
-        if (i < nbins) {
-            uint32_t c = g.hist[i];
-            part += c;
-            if (c) { key = ((uint64_t)c << 16) | i; used++; }
-            A.lenS[i] = 0;
-            cw[i] = 0;
-            mycount = c;
-        }
-        if (small) mykey = key;
-        else A.keys[i] = key;
+    uint32_t used = 0, mycount = 0, maxc = 0;
+    for (uint32_t i = tid; i < nbins; i += kCbThreads) {
+        const uint32_t c = g.hist[i];
+        part += c;
+        used += c != 0;
+        maxc = c > maxc ? c : maxc;
+        A.lenS[i] = 0;
+        mycount = c;
+        if (small && c) mykey = ((uint64_t)c << 16) | i;
     }
     for (int o = 16; o; o >>= 1) {
         part += __shfl_xor_sync(0xFFFFFFFFu, part, o);
         used += __shfl_xor_sync(0xFFFFFFFFu, used, o);
+        maxc = max(maxc, __shfl_xor_sync(0xFFFFFFFFu, maxc, o));
     }
-    if (lane == 0) { atomicAdd((unsigned long long *)&s_sum, (unsigned long long)part); atomicAdd(&s_m, used); }
+    if (lane == 0) {
+        atomicAdd((unsigned long long *)&s_sum, (unsigned long long)part);
+        atomicAdd(&s_m, used);
+        atomicMax(&s_maxc, maxc);
+    }
     __syncthreads();
     const bool overflow = s_sum >= (1ull << 32);
     const uint32_t m = overflow ? 0 : s_m;
@@ -221,25 +319,7 @@ __device__ __forceinline__ void codebook_body(const CbArgs &g, uint8_t *arrays) 
             __syncthreads();
             if (tid < P) A.keys[tid] = mykey;
         } else {
-            // passes of stride >= 32 exchange through shared memory with a
-            // barrier each; for every k, all strides below 32 run as warp
-            // shuffles in one pass over the thread's elements
-            for (uint32_t k = 2; k <= P; k <<= 1) {
-                for (uint32_t j = k >> 1; j >= 32; j >>= 1) {
-                    for (uint32_t i = tid; i < P / 2; i += kCbThreads) {
-                        uint32_t lo = 2 * i - (i & (j - 1));
-                        uint32_t hi = lo + j;
-                        uint64_t x = A.keys[lo], y = A.keys[hi];
-                        bool up = (lo & k) == 0;
-                        if ((x > y) == up) { A.keys[lo] = y; A.keys[hi] = x; }
-                    }
-                    __syncthreads();
-                }
-                const uint32_t jmax = (k >> 1) < 16 ? (k >> 1) : 16;
-                for (uint32_t e = tid; e < P; e += kCbThreads)
-                    A.keys[e] = bitonic_warp_stages(A.keys[e], e, k, jmax);
-                __syncthreads();
-            }
+            radix_sort_keys(g.hist, nbins, m, s_maxc, A.keys, P, s_rh, s_wsum);
         }
         __syncthreads();
         for (uint32_t i = tid; i < m; i += kCbThreads) A.wL[i] = (uint32_t)(A.keys[i] >> 16);
@@ -253,10 +333,13 @@ __device__ __forceinline__ void codebook_body(const CbArgs &g, uint8_t *arrays) 
         // wI[ih, it)) and the writes (wI[it, it + pairs), parent) never
         // overlap, so one named barrier per round suffices.
         const uint32_t rt = m <= 2048 ? 256u : (m <= 16384 ? 512u : (uint32_t)kCbThreads);
+        const bool rev = m > kCbRevDepth;      // implies nbins > kCbSmemBins: rstart exists
         if (tid < rt) {
             constexpr uint64_t kNone = 1ull << 33;     // above every weight (totals are < 2^32)
-            uint32_t c = 0, ih = 0, it = 0;
+            uint32_t c = 0, ih = 0, it = 0, round = 0;
             while ((m - c) + (it - ih) >= 2) {
+                if (rev && tid == 0) A.rstart[round] = it;
+                round++;
                 // t: the two lightest nodes, a leaf first on equal weight
                 const uint64_t a0 = c < m ? A.wL[c] : kNone, a1 = c + 1 < m ? A.wL[c + 1] : kNone;
                 const uint64_t b0 = ih < it ? A.wI[ih] : kNone, b1 = ih + 1 < it ? A.wI[ih + 1] : kNone;
@@ -299,17 +382,37 @@ __device__ __forceinline__ void codebook_body(const CbArgs &g, uint8_t *arrays) 
                 it += pairs;
                 asm volatile("bar.sync 1, %0;" ::"r"(rt) : "memory");
             }
+            if (tid == 0) s_rounds = round;
         }
         __syncthreads();
 
-        // ---- lengths: parent links from each leaf to the root (joined node m - 2)
-        const uint32_t root = 2 * m - 2;
+        // ---- lengths: parent links from each leaf to the root (joined node m - 2).
+        // Large trees (their links in L2) take the joined nodes' depths round
+        // by round in reverse instead: a parent is always made in a later round.
         uint32_t bad = 0;
-        for (uint32_t v = tid; v < m; v += kCbThreads) {
-            uint32_t d = 0, x = v;
-            while (x != root && d <= HUFF_MAX_LEN) { x = A.parent[x]; d++; }
-            if (d > HUFF_MAX_LEN) { bad = 1; d = HUFF_MAX_LEN; }
-            A.lenS[(uint32_t)(A.keys[v] & 0xFFFF)] = (uint8_t)d;
+        if (!rev) {
+            const uint32_t root = 2 * m - 2;
+            for (uint32_t v = tid; v < m; v += kCbThreads) {
+                uint32_t d = 0, x = v;
+                while (x != root && d <= HUFF_MAX_LEN) { x = A.parent[x]; d++; }
+                if (d > HUFF_MAX_LEN) { bad = 1; d = HUFF_MAX_LEN; }
+                A.lenS[(uint32_t)(A.keys[v] & 0xFFFF)] = (uint8_t)d;
+            }
+        } else {
+            const uint32_t nI = m - 1, rounds = s_rounds;
+            if (tid == 0) A.depthI[nI - 1] = 0;
+            __syncthreads();
+            for (int r = (int)rounds - 1; r >= 0; r--) {
+                const uint32_t j0 = A.rstart[r], j1 = r + 1 < (int)rounds ? A.rstart[r + 1] : nI;
+                for (uint32_t j = j0 + tid; j < j1; j += kCbThreads)
+                    if (j != nI - 1) A.depthI[j] = A.depthI[A.parent[m + j] - m] + 1;
+                __syncthreads();
+            }
+            for (uint32_t v = tid; v < m; v += kCbThreads) {
+                uint32_t d = A.depthI[A.parent[v] - m] + 1;
+                if (d > HUFF_MAX_LEN) { bad = 1; d = HUFF_MAX_LEN; }
+                A.lenS[(uint32_t)(A.keys[v] & 0xFFFF)] = (uint8_t)d;
+            }
         }
         if (bad) s_bad = 1;
     } else if (m == 1) {
@@ -326,16 +429,21 @@ __device__ __forceinline__ void codebook_body(const CbArgs &g, uint8_t *arrays) 
     // ---- canonical codewords, First, Entry, reverse codebook.  Ids are taken
     // in slices of kCbThreads; within a slice, a warp match gives each id its
     // rank among the warp's ids of equal length, and a per-length scan over
-    // the warps (one warp per length) its rank in the slice.
+    // the warps (one warp per length, lengths 1..lmax) its rank in the slice.
+    // Each warp clears and fills its own row of s_wcnt, so a slice needs two
+    // barriers.  Every id's cw is written (0 when unused).
     uint32_t l_mine = 0, rank_w = 0;
-    auto slice_ranks = [&](uint32_t base) {
+    auto slice_ranks = [&](uint32_t base, uint32_t lmax) {
+        __syncwarp();
+        for (uint32_t l = lane; l <= lmax; l += 32) s_wcnt[warp][l] = 0;
+        __syncwarp();
         const uint32_t id = base + tid;
         l_mine = id < nbins ? A.lenS[id] : 0;
         const uint32_t peers = __match_any_sync(0xFFFFFFFFu, l_mine);
         rank_w = __popc(peers & ((1u << lane) - 1));
-        if (rank_w == 0) s_wcnt[warp][l_mine] = __popc(peers);
+        if (rank_w == 0 && l_mine) s_wcnt[warp][l_mine] = __popc(peers);
         __syncthreads();
-        for (uint32_t l = warp + 1; l <= HUFF_MAX_LEN; l += kCbThreads / 32) {
+        for (uint32_t l = warp + 1; l <= lmax; l += kCbThreads / 32) {
             const uint32_t b = s_base[l], cnt = s_wcnt[lane][l];
             uint32_t inc = cnt;
 #pragma unroll
@@ -374,34 +482,36 @@ __device__ __forceinline__ void codebook_body(const CbArgs &g, uint8_t *arrays) 
             const uint32_t rank = s_wcnt[warp][l_mine] + rank_w;
             cw[id] = (s_first[l_mine] + rank) | ((uint64_t)l_mine << HUFF_CW_LEN_SHIFT);
             sorted_syms[s_entry[l_mine] + rank] = id;
+        } else if (id < nbins) {
+            cw[id] = 0;
         }
     };
     uint64_t tb = 0;
     if (nbins <= kCbThreads) {
         // one slice: its per-length totals are the counts
-        slice_ranks(0);
+        slice_ranks(0, HUFF_MAX_LEN);
         if (l_mine) tb = (uint64_t)l_mine * mycount;
         if (tid >= 1 && tid <= HUFF_MAX_LEN) s_count[tid] = s_base[tid];
         __syncthreads();
         first_entry();
         write_codes(0);
     } else {
-        for (uint32_t i = tid; i < nbins; i += kCbThreads) {
-            uint32_t l = A.lenS[i];
+        // counts per length: one shared atomic per warp and length
+        for (uint32_t base = 0; base < nbins; base += kCbThreads) {
+            const uint32_t i = base + tid;
+            const uint32_t l = i < nbins ? A.lenS[i] : 0u;
+            const uint32_t peers = __match_any_sync(0xFFFFFFFFu, l);
             if (l) {
-                atomicAdd(&s_count[l], 1u);
+                if (__popc(peers & ((1u << lane) - 1)) == 0) atomicAdd(&s_count[l], (uint32_t)__popc(peers));
                 tb += (uint64_t)l * g.hist[i];
             }
         }
         __syncthreads();
         first_entry();
+        const uint32_t lmax = s_maxlen;
         for (uint32_t base = 0; base < nbins; base += kCbThreads) {
-            slice_ranks(base);
+            slice_ranks(base, lmax);
             write_codes(base);
-            __syncthreads();
-            for (uint32_t i = tid; i < (kCbThreads / 32) * (HUFF_MAX_LEN + 1); i += kCbThreads)
-                (&s_wcnt[0][0])[i] = 0;
-            __syncthreads();
         }
     }
     for (int o = 16; o; o >>= 1) tb += __shfl_xor_sync(0xFFFFFFFFu, tb, o);
