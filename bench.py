@@ -36,6 +36,8 @@ WORKLOADS = {
     "served": (None, None, "Poisson arrivals at --rate req/s for --duration s; half u8 Zipf(1.2) over 256 ids, "
                            "half u16 Gaussian/Laplace(512, scale log-uniform in [1, 64]) over 1024 bins; n log-uniform "
                            "in [16384, 67108864]; payloads drawn on the device before arrival; seed 5"),
+    "large_alphabet": (1 << 26, 65536, "u32 Zipf(s=1.1) over 8,192 and 65,536 ids mapped through a seeded "
+                                       "permutation, 67,108,864 symbols per alphabet, seed 3"),
     "batched_fields": (None, 1024, "512 u16 fields, n log-uniform in [65536, 16777216], Laplace(512, b ~ U[0.5, 16]) "
                                    "over 1024 bins, seed 4 (field j: stream j, size/scale from stream 10000+j)"),
 }
@@ -48,6 +50,8 @@ def make_input(name: str, n: int | None = None, rank: int = 0) -> np.ndarray:
         return synth.laplace_field(n or 512 ** 3, seed=1, stream=rank)
     if name == "small_field":
         return synth.gaussian_field(n or (1 << 20), seed=0)
+    if name == "large_alphabet":
+        return synth.zipf_field(n or (1 << 26), 65536)
     raise ValueError(name)
 
 
@@ -213,7 +217,8 @@ def run_reference(args, world, rank):
         "metric": {"batched_fields": "huffman_batched_encode_input_GBps",
                    "served": "huffman_served_encode_input_GBps"}.get(name, "huffman_encode_input_GBps"), "value": round(value, 4), "unit": "GB/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16", "data": "synthetic",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32" if name == "large_alphabet" else "u16", "data": "synthetic",
         "config": {"workload": name, "n": n_full, "nbins": nbins, "input": desc},
         "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": samp, "value": round(value, 4), "unit": "GB/s"},
         "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -375,6 +380,130 @@ def run_ours(args, world, rank, local):
                                "traffic": load_traffic("hist_kernel") if name == "hpc_field" else None},
         "e2e": {"value": round(e2e_val, 3), "unit": "GB/s", "h2d_bytes_per_step": in_bytes,
                 "d2h_bytes_per_step": out_bytes + off_bytes + 8},
+        "gpu_launches": launches,
+        "cpu_baseline": cpu,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- large alphabets
+
+def run_large_alphabet(args, world, rank, local):
+    """The large-alphabet stress: 67,108,864 u32 Zipf(1.1) symbols over 8,192
+    and then 65,536 ids, each through histogram -> codebook -> encode, with
+    the codebook construction timed on its own.  A step is both alphabets."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2010_10039_gb300 as huff
+    from paper_2010_10039_gb300 import synth
+
+    torch.cuda.set_device(local)
+    n = WORKLOADS["large_alphabet"][0]
+    alphabets = (8192, 65536)
+    params = {"chunk_log2": args.chunk_log2}
+    fields = []
+    for K in alphabets:
+        sym = synth.draw_device(3, rank, n, synth.cdf_table(synth.zipf_pmf(K, 1.1)), 4,
+                                mapping=synth.permutation(3, K))
+        fields.append((K, sym, huff.Pipeline(n, K, params)))
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        for K, sym, pipe in fields:
+            pipe.run(sym)
+    torch.cuda.synchronize()
+    for K, sym, pipe in fields:
+        st = pipe.status()
+        if st != 0:
+            raise RuntimeError(f"{K} bins: device status {huff.STATUS.get(st, st)}")
+
+    steps = args.steps
+    ev = {K: [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)] for K in alphabets}
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    l0 = huff.huff_launch_count()
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for k in range(steps):
+        for K, sym, pipe in fields:
+            e = ev[K][k]
+            e[0].record(stream)
+            pipe.run(sym, stages=("hist",))
+            e[1].record(stream)
+            pipe.run(sym, stages=("codebook",))
+            e[2].record(stream)
+            pipe.run(sym, stages=("encode",))
+            e[3].record(stream)
+    stop.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = huff.huff_launch_count() - l0
+    clk = clocks.stop()
+    ms_step = max_over_ranks(start.elapsed_time(stop) / steps, world)
+    peak, peak_kind = load_peak()
+    in_bytes = n * 4
+    per = {}
+    enc_total_ms = 0.0
+    for K, sym, pipe in fields:
+        st = pipe.status()
+        if st != 0:
+            raise RuntimeError(f"{K} bins: device status {huff.STATUS.get(st, st)}")
+        hist_ms = statistics.mean(ev[K][k][0].elapsed_time(ev[K][k][1]) for k in range(steps))
+        cb_ms = statistics.mean(ev[K][k][1].elapsed_time(ev[K][k][2]) for k in range(steps))
+        enc_ms = statistics.mean(ev[K][k][2].elapsed_time(ev[K][k][3]) for k in range(steps))
+        enc_total_ms += enc_ms
+        total_bits = int(pipe.total_bits.item())
+        max_len = int(pipe.codebook[4:8].view(torch.int32).item())
+        nch = (n + (1 << args.chunk_log2) - 1) >> args.chunk_log2
+        enc_alg = in_bytes + (total_bits + 31) // 32 * 4 + (nch + 1) * 8
+        per[str(K)] = {
+            "codebook_us": round(cb_ms * 1e3, 2),
+            "stages_ms": {"histogram": round(hist_ms, 5), "codebook": round(cb_ms, 5), "encode": round(enc_ms, 5)},
+            "step_GBps": round(in_bytes / ((hist_ms + cb_ms + enc_ms) * 1e-3) / 1e9, 3),
+            "encode_roofline": {"bound": "hbm", "achieved": round(enc_alg / (enc_ms * 1e-3) / 1e9, 2),
+                                "peak": peak, "unit": "GB/s",
+                                "frac": round(enc_alg / (enc_ms * 1e-3) / 1e9 / peak, 4),
+                                "traffic": None, "algorithmic_bytes": enc_alg},
+            "avg_bits": round(total_bits / n, 4),
+            "max_len": max_len,
+        }
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        ns = 1 << 22
+        cpu = {}
+        for K in alphabets:
+            symh = synth.zipf_field(ns, K)
+            t0 = time.perf_counter()
+            h = oracle.histogram(symh, K)
+            t1 = time.perf_counter()
+            book = oracle.codebook(h)
+            t2 = time.perf_counter()
+            oracle.encode(symh, book, chunk_log2=10)
+            t3 = time.perf_counter()
+            cpu[str(K)] = {"value": round(ns * 4 / (t3 - t0) / 1e9, 4), "codebook_us": round((t2 - t1) * 1e6, 1)}
+        cpu = {"value": round(2 * ns * 4 / sum(ns * 4 / v["value"] / 1e9 for v in cpu.values()) / 1e9, 4),
+               "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": f"first {ns} symbols of each alphabet's field, histogram+codebook+encode, 1 thread",
+               "per_alphabet": cpu}
+    value = world * len(alphabets) * in_bytes / (ms_step * 1e-3) / 1e9
+    line = {
+        "metric": "huffman_encode_input_GBps", "value": round(value, 3), "unit": "GB/s", "n_gpus": world,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "large_alphabet", "n": n, "alphabets": list(alphabets),
+                   "input": WORKLOADS["large_alphabet"][2], "chunk_log2": args.chunk_log2,
+                   "l2": "inputs larger than L2 (268 MB per field)", "parallelism": f"replicas{world}"},
+        "alphabets": per,
+        "e2e": None,
         "gpu_launches": launches,
         "cpu_baseline": cpu,
         "clocks": clk,
@@ -822,6 +951,8 @@ def main():
         run_batched(args, world, rank, local)
     elif args.workload == "served":
         run_served(args, world, rank, local)
+    elif args.workload == "large_alphabet":
+        run_large_alphabet(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

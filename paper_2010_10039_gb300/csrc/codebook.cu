@@ -41,6 +41,8 @@ constexpr int kCbThreads = 1024;
 constexpr uint32_t kCbSmemBins = 4096;     // arrays live in shared memory up to this alphabet
 constexpr uint32_t kCbRevDepth = 16384;    // above this many used symbols, depths by a per-round pass
 constexpr uint32_t kRadixDigits = 256;     // 8-bit digits of the large-alphabet sort
+constexpr uint32_t kRhStride = 34;         // u16 per digit row of the counting table: 17 words, odd, so
+                                           // one warp's distinct digits fall in distinct banks
 
 struct CbArrays {
     uint64_t *keys;     // 2P      sort keys (count << 16 | id); the two halves are the
@@ -120,87 +122,141 @@ __device__ __forceinline__ uint64_t bitonic_sort_regs(uint64_t x, uint32_t P, ui
     return x;
 }
 
+// ---- stable counting passes (one CTA)
+// A pass places elements 0..len-1 that carry a digit (0..kRadixDigits-1) in
+// digit-major, then element order.  Warp w owns a contiguous segment of the
+// elements; its per-digit counts rh[digit][w], scanned in digit-major order,
+// give its first slot for each digit, and the lanes of one step rank among
+// themselves by a warp match.  Counts and slots stay below 65,536 (len is at
+// most HUFF_MAX_BINS), so the table is u16, its rows padded to kRhStride.
+// elem(i) returns an element, four at a time so that their loads overlap.
+
+struct CpElem {
+    bool valid;         // carries a digit
+    uint32_t digit;
+    uint64_t payload;
+};
+
+__device__ __forceinline__ void cp_segment(uint32_t len, uint32_t &begin, uint32_t &end) {
+    const uint32_t warp = threadIdx.x >> 5;
+    const uint32_t seg = (((len + 31) / 32) + 31) & ~31u;
+    begin = warp * seg < len ? warp * seg : len;
+    end = begin + seg < len ? begin + seg : len;
+}
+
+// Counts, then scans rh into first slots; totals[d] (d < ntotals) receives the
+// number of elements with digit d.  Ends with a barrier.
+template <typename Elem>
+__device__ void cpass_count(uint32_t len, Elem elem, uint16_t (*rh)[kRhStride], uint32_t *wsum, uint32_t *totals,
+                            uint32_t ntotals) {
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t lt = (1u << lane) - 1;
+    uint32_t begin, end;
+    cp_segment(len, begin, end);
+    for (uint32_t i = tid; i < kRadixDigits * kRhStride; i += kCbThreads) (&rh[0][0])[i] = 0;
+    __syncthreads();
+    for (uint32_t b = begin; b < end; b += 128) {
+        CpElem e[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const uint32_t i = b + 32 * q + lane;
+            e[q] = i < end ? elem(i) : CpElem{false, 0u, 0ull};
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const uint32_t peers = __match_any_sync(0xFFFFFFFFu, e[q].valid ? e[q].digit : 0x10000u);
+            if (e[q].valid && __popc(peers & lt) == 0) rh[e[q].digit][warp] += (uint16_t)__popc(peers);
+        }
+    }
+    __syncthreads();
+    for (uint32_t d = tid; d < ntotals; d += kCbThreads) {
+        uint32_t t = 0;
+        for (uint32_t w = 0; w < 32; w++) t += rh[d][w];
+        totals[d] = t;
+    }
+    // exclusive scan in digit-major order: eight entries per thread (digit
+    // tid / 4, warps 8 * (tid % 4) ..)
+    uint16_t *row = &rh[tid >> 2][8 * (tid & 3)];
+    uint32_t v[8], sum = 0;
+#pragma unroll
+    for (int q = 0; q < 8; q++) { v[q] = row[q]; sum += v[q]; }
+    uint32_t inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    uint32_t wbase = 0;
+    for (uint32_t w = 0; w < warp; w++) wbase += wsum[w];
+    uint32_t run = wbase + inc - sum;
+#pragma unroll
+    for (int q = 0; q < 8; q++) { row[q] = (uint16_t)run; run += v[q]; }
+    __syncthreads();
+}
+
+// Hands every element with a digit to place(slot, payload) and every other
+// one to skip(payload), in the same element order as cpass_count.  Ends with
+// a barrier.
+template <typename Elem, typename Place, typename Skip>
+__device__ void cpass_scatter(uint32_t len, Elem elem, Place place, Skip skip, uint16_t (*rh)[kRhStride]) {
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1;
+    uint32_t begin, end;
+    cp_segment(len, begin, end);
+    for (uint32_t b = begin; b < end; b += 128) {
+        CpElem e[4];
+        bool in[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const uint32_t i = b + 32 * q + lane;
+            in[q] = i < end;
+            e[q] = in[q] ? elem(i) : CpElem{false, 0u, 0ull};
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const uint32_t peers = __match_any_sync(0xFFFFFFFFu, e[q].valid ? e[q].digit : 0x10000u);
+            const uint32_t rank = __popc(peers & lt);
+            const uint32_t slot = e[q].valid ? rh[e[q].digit][warp] : 0u;
+            __syncwarp();
+            if (e[q].valid && rank == 0) rh[e[q].digit][warp] = (uint16_t)(slot + __popc(peers));
+            __syncwarp();
+            if (e[q].valid) place(slot + rank, e[q].payload);
+            else if (in[q]) skip(e[q].payload);
+        }
+    }
+    __syncthreads();
+}
+
 // Stable LSD radix sort, by count, of the used bins of hist[nbins] into
 // buf[0, m) as keys count << 16 | id.  Bins enter in id order, so equal counts
 // stay in id order and the result is the (count, id) order.  8-bit digits,
 // as many passes as maxcount has digits; pass 0 reads the histogram and drops
 // unused bins, and the passes alternate between buf[0, P) and buf[P, 2P) so
-// that the last one lands in buf[0, P).  Warp w owns a contiguous segment of
-// each pass's input; its per-digit counts (rh[digit][w]), scanned in
-// digit-major order, give its first slot for each digit, and the lanes of one
-// step rank among themselves by a warp match.  Every count and slot is below
-// 65,536, so they are held as u16.
+// that the last one lands in buf[0, P).
 __device__ void radix_sort_keys(const uint32_t *hist, uint32_t nbins, uint32_t m, uint32_t maxcount, uint64_t *buf,
-                                uint32_t P, uint16_t (*rh)[32], uint32_t *wsum) {
-    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t lt = (1u << lane) - 1;
+                                uint32_t P, uint16_t (*rh)[kRhStride], uint32_t *wsum) {
     const uint32_t bits = 32 - __clz(maxcount);
     const uint32_t npass = bits > 8 ? (bits + 7) / 8 : 1;
     for (uint32_t pass = 0; pass < npass; pass++) {
         const uint32_t shift = 16 + 8 * pass;
         const uint64_t *src = buf + ((npass - pass) & 1) * P;
         uint64_t *dst = buf + ((npass - 1 - pass) & 1) * P;
-        const uint32_t len = pass == 0 ? nbins : m;
-        const uint32_t seg = (((len + 31) / 32) + 31) & ~31u;
-        const uint32_t begin = warp * seg < len ? warp * seg : len;
-        const uint32_t end = begin + seg < len ? begin + seg : len;
-        for (uint32_t i = tid; i < kRadixDigits * 32; i += kCbThreads) (&rh[0][0])[i] = 0;
-        __syncthreads();
-        // one step: four loads in flight, then the four groups of 32 in order
-        auto step = [&](uint32_t b, bool scatter) {
-            uint64_t key[4];
-            bool valid[4];
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-                const uint32_t i = b + 32 * q + lane;
-                valid[q] = i < end;
-                if (pass == 0) {
-                    const uint32_t c = valid[q] ? hist[i] : 0u;
-                    valid[q] = c != 0;
-                    key[q] = ((uint64_t)c << 16) | i;
-                } else {
-                    key[q] = valid[q] ? src[i] : 0ull;
-                }
+        auto elem = [&](uint32_t i) -> CpElem {
+            uint64_t key;
+            if (pass == 0) {
+                const uint32_t c = hist[i];
+                key = ((uint64_t)c << 16) | i;
+                if (c == 0) return CpElem{false, 0u, key};
+            } else {
+                key = src[i];
             }
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-                const uint32_t digit = valid[q] ? (uint32_t)(key[q] >> shift) & (kRadixDigits - 1) : 0x10000u;
-                const uint32_t peers = __match_any_sync(0xFFFFFFFFu, digit);
-                const uint32_t rank = __popc(peers & lt);
-                if (!scatter) {
-                    if (valid[q] && rank == 0) rh[digit][warp] += (uint16_t)__popc(peers);
-                } else {
-                    const uint32_t slot = valid[q] ? rh[digit][warp] : 0u;
-                    __syncwarp();
-                    if (valid[q] && rank == 0) rh[digit][warp] = (uint16_t)(slot + __popc(peers));
-                    __syncwarp();
-                    if (valid[q]) dst[slot + rank] = key[q];
-                }
-            }
+            return CpElem{true, (uint32_t)(key >> shift) & (kRadixDigits - 1), key};
         };
-        for (uint32_t b = begin; b < end; b += 128) step(b, false);
-        __syncthreads();
-        // exclusive scan of rh in digit-major order: eight entries per thread
-        uint16_t *flat = &rh[0][0];
-        uint32_t v[8], sum = 0;
-#pragma unroll
-        for (int q = 0; q < 8; q++) { v[q] = flat[8 * tid + q]; sum += v[q]; }
-        uint32_t inc = sum;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
-            if (lane >= o) inc += y;
-        }
-        if (lane == 31) wsum[warp] = inc;
-        __syncthreads();
-        uint32_t wbase = 0;
-        for (uint32_t w = 0; w < warp; w++) wbase += wsum[w];
-        uint32_t run = wbase + inc - sum;
-#pragma unroll
-        for (int q = 0; q < 8; q++) { flat[8 * tid + q] = (uint16_t)run; run += v[q]; }
-        __syncthreads();
-        for (uint32_t b = begin; b < end; b += 128) step(b, true);
-        __syncthreads();
+        const uint32_t len = pass == 0 ? nbins : m;
+        cpass_count(len, elem, rh, wsum, nullptr, 0);
+        cpass_scatter(len, elem, [&](uint32_t slot, uint64_t key) { dst[slot] = key; }, [](uint64_t) {}, rh);
     }
 }
 
@@ -261,7 +317,7 @@ __device__ __forceinline__ void codebook_body(const CbArgs &g, uint8_t *arrays) 
     __shared__ uint64_t s_sum, s_tbits;
     __shared__ uint32_t s_m, s_maxlen, s_bad, s_maxc, s_rounds;
     __shared__ uint32_t s_wsum[kCbThreads / 32];
-    __shared__ uint16_t s_rh[kRadixDigits][32];
+    __shared__ uint16_t s_rh[kRadixDigits][kRhStride];
     __shared__ uint32_t s_count[HUFF_MAX_LEN + 1];
     __shared__ uint32_t s_base[HUFF_MAX_LEN + 1];
     __shared__ uint64_t s_first[HUFF_MAX_LEN + 1];
@@ -496,22 +552,28 @@ __device__ __forceinline__ void codebook_body(const CbArgs &g, uint8_t *arrays) 
         first_entry();
         write_codes(0);
     } else {
-        // counts per length: one shared atomic per warp and length
-        for (uint32_t base = 0; base < nbins; base += kCbThreads) {
-            const uint32_t i = base + tid;
-            const uint32_t l = i < nbins ? A.lenS[i] : 0u;
-            const uint32_t peers = __match_any_sync(0xFFFFFFFFu, l);
-            if (l) {
-                if (__popc(peers & ((1u << lane) - 1)) == 0) atomicAdd(&s_count[l], (uint32_t)__popc(peers));
-                tb += (uint64_t)l * g.hist[i];
-            }
-        }
+        // one stable counting pass by length over the ids: an id's slot in
+        // (length, id) order is its sorted_syms index, and slot - entry[l]
+        // its rank among the codewords of length l
+        auto elem = [&](uint32_t i) -> CpElem {
+            const uint32_t l = A.lenS[i];
+            return CpElem{l != 0, l, ((uint64_t)l << 32) | i};
+        };
+        cpass_count(nbins, elem, s_rh, s_wsum, s_count, HUFF_MAX_LEN + 1);
+        if (tid == 0) s_count[0] = 0;
         __syncthreads();
         first_entry();
-        const uint32_t lmax = s_maxlen;
-        for (uint32_t base = 0; base < nbins; base += kCbThreads) {
-            slice_ranks(base, lmax);
-            write_codes(base);
+        cpass_scatter(
+            nbins, elem,
+            [&](uint32_t slot, uint64_t pl) {
+                const uint32_t l = (uint32_t)(pl >> 32), id = (uint32_t)pl;
+                cw[id] = (s_first[l] + (slot - s_entry[l])) | ((uint64_t)l << HUFF_CW_LEN_SHIFT);
+                sorted_syms[slot] = id;
+            },
+            [&](uint64_t pl) { cw[(uint32_t)pl] = 0; }, s_rh);
+        for (uint32_t i = tid; i < nbins; i += kCbThreads) {
+            const uint32_t l = A.lenS[i];
+            if (l) tb += (uint64_t)l * g.hist[i];
         }
     }
     for (int o = 16; o; o >>= 1) tb += __shfl_xor_sync(0xFFFFFFFFu, tb, o);
