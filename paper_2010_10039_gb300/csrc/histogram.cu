@@ -9,8 +9,11 @@
 // warp counts into its own replica (same-bin conflicts stay inside one warp),
 // the replicas are folded once per CTA and only nonzero bins reach the global
 // histogram.  Alphabets too large for 32-bit counters in shared memory use
-// packed 16-bit counters (bins k and k + 32768 share a word) that are flushed
-// to the global histogram before any of them can wrap.
+// packed 16-bit counters (bins k and k + 32768 share a word).  The increment
+// that takes a counter to 0x8000 moves 0x8000 to the global bin; with a
+// barrier every 32,768 symbols of the CTA, every counter is at most 0x7FFF at
+// each barrier, so none can pass 0xFFFF in between, and the table is folded
+// into the global histogram once, at the end.
 #include "kernels.cuh"
 
 namespace huff {
@@ -61,17 +64,42 @@ struct HistArgs {
 // slots (mask + 1 >= nbins) and symbols are masked into them; `seen` ORs the
 // symbols, so a symbol beyond the slots is caught after the loop, and one in
 // [nbins, mask] leaves a count in a slot past nbins (both are range errors).
-template <bool PACKED>
-__device__ __forceinline__ void count_one(uint32_t *h, uint32_t s, uint32_t mask, uint32_t &seen) {
+// Packed counters with CARRY: the increment that takes a 16-bit counter from
+// 0x7FFF to 0x8000 (exactly one per crossing, atomics being ordered) takes
+// 0x8000 back out and adds it to the global bin.  A slot at or past nbins is a
+// range error (*bad); its count is dropped.
+struct Carry {
+    uint32_t *hist;
+    uint32_t nbins;
+};
+
+template <bool PACKED, bool CARRY = false>
+__device__ __forceinline__ void count_one(uint32_t *h, uint32_t s, uint32_t mask, uint32_t &seen,
+                                          const Carry &cy = Carry{nullptr, 0}, uint32_t *bad = nullptr) {
     seen |= s;
-    if (PACKED) atomicAdd(h + (s & (kPackedWords - 1)), 1u << (((s & mask) >> 15) << 4));
-    else atomicAdd(h + (s & mask), 1u);
+    if (PACKED) {
+        const uint32_t sh = ((s & mask) >> 15) << 4;
+        uint32_t *w = h + (s & (kPackedWords - 1));
+        if (CARRY) {
+            const uint32_t old = atomicAdd(w, 1u << sh);
+            if (((old >> sh) & 0xFFFFu) == 0x7FFFu) {
+                atomicSub(w, 0x8000u << sh);
+                if ((s & mask) < cy.nbins) atomicAdd(cy.hist + (s & mask), 0x8000u);
+                else *bad = 1;
+            }
+        } else {
+            atomicAdd(w, 1u << sh);
+        }
+    } else {
+        atomicAdd(h + (s & mask), 1u);
+    }
 }
 
-template <typename Sym, bool PACKED>
-__device__ __forceinline__ void count_vec(uint32_t *h, const uint4 &v, uint32_t mask, uint32_t &seen) {
+template <typename Sym, bool PACKED, bool CARRY = false>
+__device__ __forceinline__ void count_vec(uint32_t *h, const uint4 &v, uint32_t mask, uint32_t &seen,
+                                          const Carry &cy = Carry{nullptr, 0}, uint32_t *bad = nullptr) {
 #pragma unroll
-    for (int j = 0; j < SymVec<Sym>::N; j++) count_one<PACKED>(h, SymVec<Sym>::get(v, j), mask, seen);
+    for (int j = 0; j < SymVec<Sym>::N; j++) count_one<PACKED, CARRY>(h, SymVec<Sym>::get(v, j), mask, seen, cy, bad);
 }
 
 // Folds the shared-memory counts into the global histogram; counts in slots
@@ -116,38 +144,35 @@ __global__ void __launch_bounds__(kHistThreads, 2) hist_kernel(HistArgs a) {
     const uint4 *vec = reinterpret_cast<const uint4 *>(a.base + a.head * sizeof(Sym));
     constexpr uint64_t kRound = 2ull * kHistThreads;              // vectors per CTA round
     constexpr uint32_t kSymsPerRound = kRound * SymVec<Sym>::N;
-    // packed counters: flush before any 16-bit field can reach 65536
-    constexpr uint32_t kRoundsPerEpoch = PACKED ? 65535u / kSymsPerRound : 0xFFFFFFFFu;
+    // packed counters: a barrier at least every 32,768 symbols of the CTA (an
+    // epoch), so that a counter at most 0x7FFF at its start stays below 0x10000
+    constexpr uint32_t kRoundsPerEpoch = PACKED ? 32768u / kSymsPerRound : 0xFFFFFFFFu;
+    static_assert(!PACKED || kRoundsPerEpoch >= 1, "a round must fit in an epoch");
+    const Carry cy{a.hist, a.nbins};
     const uint64_t nrounds = (a.nvec + kRound - 1) / kRound;
     uint32_t since = 0;
     for (uint64_t r = blockIdx.x; r < nrounds; r += gridDim.x) {
         const uint64_t i0 = r * kRound + threadIdx.x, i1 = i0 + kHistThreads;
         if (i1 < a.nvec) {
             uint4 v0 = vec[i0], v1 = vec[i1];
-            count_vec<Sym, PACKED>(my, v0, mask, seen);
-            count_vec<Sym, PACKED>(my, v1, mask, seen);
+            count_vec<Sym, PACKED, PACKED>(my, v0, mask, seen, cy, &bad);
+            count_vec<Sym, PACKED, PACKED>(my, v1, mask, seen, cy, &bad);
         } else if (i0 < a.nvec) {
-            count_vec<Sym, PACKED>(my, vec[i0], mask, seen);
+            count_vec<Sym, PACKED, PACKED>(my, vec[i0], mask, seen, cy, &bad);
         }
         if (PACKED && ++since == kRoundsPerEpoch) {
-            __syncthreads();
-            hist_flush<true>(hsm, a.hist, a.nbins, a.mask, a.nrep, a.stride, bad);
             __syncthreads();
             since = 0;
         }
     }
-    if (PACKED) {
-        __syncthreads();
-        hist_flush<true>(hsm, a.hist, a.nbins, a.mask, a.nrep, a.stride, bad);
-        __syncthreads();
-    }
+    if (PACKED) __syncthreads();     // the head and tail below are an epoch of their own
     // head (before the first aligned address) and tail (after the last whole vector)
     const uint64_t tail0 = a.head + a.nvec * SymVec<Sym>::N;
     const Sym *sp = reinterpret_cast<const Sym *>(a.base);
     const uint64_t nrest = a.head + (a.n - tail0);
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nrest; i += (uint64_t)gridDim.x * blockDim.x) {
         uint64_t idx = i < a.head ? i : tail0 + (i - a.head);
-        count_one<PACKED>(my, sp[idx], mask, seen);
+        count_one<PACKED, PACKED>(my, sp[idx], mask, seen, cy, &bad);
     }
     __syncthreads();
     hist_flush<PACKED>(hsm, a.hist, a.nbins, a.mask, a.nrep, a.stride, bad);

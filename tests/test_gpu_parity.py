@@ -249,6 +249,26 @@ def test_hpc_field_full_size():
     _full_check(sym, 1024)
 
 
+@pytest.mark.parametrize("width", [2, 4])
+def test_packed_histogram_heavy_bins(width):
+    """Alphabets above 16,384 bins count in packed 16-bit shared counters
+    (bins k and k + 32768 share a word) that carry 0x8000 to the global bin.
+    Here one bin takes most of the field, so every CTA carries it many times,
+    and the other half of the same word (bin 40000 - 32768 = 7232) and a bin
+    near the top are heavy too; the input starts off a 16-byte boundary so the
+    head and tail are counted as well."""
+    n = 20_000_000 + 13
+    rng = np.random.default_rng(77)
+    sym = np.full(n, 40000, dtype=np.uint16 if width == 2 else np.uint32)
+    sym[rng.integers(0, n, size=n // 3)] = 7232
+    sym[rng.integers(0, n, size=n // 50)] = 65535
+    sym[rng.integers(0, n, size=1000)] = 3
+    r = Run(sym, 65536, offset_elems=3).histogram()
+    assert r.status() == 0
+    assert np.array_equal(r.hist_np(), oracle.histogram(sym, 65536))
+    assert np.array_equal(r.hist_np(), np.bincount(sym, minlength=65536).astype(np.uint32))
+
+
 @pytest.mark.parametrize("K", [8192, 65536])
 def test_large_alphabet_full_size(K):
     """67,108,864 u32 Zipf(1.1) symbols over 8,192 / 65,536 permuted ids, seed 3."""
