@@ -42,6 +42,7 @@ WORKLOADS = {
                                    "over 1024 bins, seed 4 (field j: stream j, size/scale from stream 10000+j)"),
 }
 BATCH_FIELDS = 512
+NOMINAL_HBM_GBPS = 8000.0     # GB300 HBM3e, nominal (the measured copy peak is the headline denominator)
 
 
 def make_input(name: str, n: int | None = None, rank: int = 0) -> np.ndarray:
@@ -167,27 +168,37 @@ def max_over_ranks(x: float, world: int) -> float:
 
 # ----------------------------------------------------------------------------- CPU oracle leg
 
+LAST_ORACLE_PARTS = {}
+
+
 def oracle_leg(name: str, n_full: int, nbins: int, max_seconds: float = 15.0):
     """Times the oracle (single thread) on a prefix of the workload; returns
-    (GB/s of input, sample description, symbols, seconds)."""
+    (GB/s of input, sample description, symbols, seconds).  The last run's
+    histogram, codebook and encode times are left in LAST_ORACLE_PARTS."""
     import oracle
     oracle.build()
-    n = min(n_full, 1 << 24)
-    sym = make_input(name, n)
-    t0 = time.perf_counter()
-    h = oracle.histogram(sym, nbins)
-    book = oracle.codebook(h)
-    oracle.encode(sym, book, chunk_log2=10)
-    dt = time.perf_counter() - t0
-    # grow the sample while the whole leg stays within the time bound
-    while n < n_full and dt * (min(n_full, 4 * n) / n) < max_seconds:
-        n = min(n_full, 4 * n)
+
+    def once(n):
         sym = make_input(name, n)
         t0 = time.perf_counter()
         h = oracle.histogram(sym, nbins)
+        t1 = time.perf_counter()
         book = oracle.codebook(h)
+        t2 = time.perf_counter()
         oracle.encode(sym, book, chunk_log2=10)
-        dt = time.perf_counter() - t0
+        t3 = time.perf_counter()
+        LAST_ORACLE_PARTS.clear()
+        LAST_ORACLE_PARTS.update({"histogram_GBps": round(sym.nbytes / (t1 - t0) / 1e9, 4),
+                                  "codebook_ms": round((t2 - t1) * 1e3, 3),
+                                  "encode_GBps": round(sym.nbytes / (t3 - t2) / 1e9, 4)})
+        return sym, t3 - t0
+
+    n = min(n_full, 1 << 24)
+    sym, dt = once(n)
+    # grow the sample while the whole leg stays within the time bound
+    while n < n_full and dt * (min(n_full, 4 * n) / n) < max_seconds:
+        n = min(n_full, 4 * n)
+        sym, dt = once(n)
     gbs = n * sym.itemsize / dt / 1e9
     return gbs, f"first {n} symbols of the workload, histogram+codebook+encode, 1 thread", n, dt
 
@@ -282,9 +293,12 @@ def run_ours(args, world, rank, local):
     if st != 0:
         raise RuntimeError(f"device status {huff.STATUS.get(st, st)}")
 
-    hist_ms = statistics.mean(ev[k][0].elapsed_time(ev[k][1]) for k in range(K))
-    cb_ms = statistics.mean(ev[k][1].elapsed_time(ev[k][2]) for k in range(K))
-    enc_ms = statistics.mean(ev[k][2].elapsed_time(ev[k][3]) for k in range(K))
+    stage_lists = {"histogram": [ev[k][0].elapsed_time(ev[k][1]) for k in range(K)],
+                   "codebook": [ev[k][1].elapsed_time(ev[k][2]) for k in range(K)],
+                   "encode": [ev[k][2].elapsed_time(ev[k][3]) for k in range(K)]}
+    hist_ms = statistics.mean(stage_lists["histogram"])
+    cb_ms = statistics.mean(stage_lists["codebook"])
+    enc_ms = statistics.mean(stage_lists["encode"])
     in_bytes = n * 2
     out_bytes = (total_bits + 31) // 32 * 4
     nch = (n + (1 << args.chunk_log2) - 1) >> args.chunk_log2
@@ -376,7 +390,8 @@ def run_ours(args, world, rank, local):
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         gbs, samp, _, _ = oracle_leg(name, n, nbins)
-        cpu = {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": samp}
+        cpu = {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": samp,
+               "parts": dict(LAST_ORACLE_PARTS), "host_cores": os.cpu_count()}
     enc_s = enc_ms * 1e-3
     line = {
         "metric": "huffman_encode_input_GBps",
@@ -396,13 +411,16 @@ def run_ours(args, world, rank, local):
                    "l2": "inputs larger than L2 (268 MB per step)", "parallelism": f"replicas{world}",
                    "avg_bits": round(total_bits / n, 4)},
         "stages_ms": {"histogram": round(hist_ms, 5), "codebook": round(cb_ms, 5), "encode": round(enc_ms, 5)},
+        "stages_ms_best": {k: round(min(v), 5) for k, v in stage_lists.items()},
+        "stages_ms_median": {k: round(statistics.median(v), 5) for k, v in stage_lists.items()},
         "encode_only_GBps": round(in_bytes / enc_s / 1e9, 3),
         "roofline": {"bound": "hbm", "kernel": "encode (a4-a6)" if args.merge == "scan" else
                      "encode, paper layout: merge + scan + gather kernels", "achieved": round(enc_alg / enc_s / 1e9, 2),
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": round(enc_alg / enc_s / 1e9 / peak, 4),
                      "traffic": load_traffic("encode_kernel") if name == "hpc_field" and args.merge == "scan" else None,
-                     "algorithmic_bytes": enc_alg},
+                     "algorithmic_bytes": enc_alg, "peak_nominal": NOMINAL_HBM_GBPS,
+                     "frac_nominal": round(enc_alg / enc_s / 1e9 / NOMINAL_HBM_GBPS, 4)},
         "roofline_histogram": {"bound": "hbm", "achieved": round(hist_alg / (hist_ms * 1e-3) / 1e9, 2),
                                "peak": peak, "unit": "GB/s",
                                "frac": round(hist_alg / (hist_ms * 1e-3) / 1e9 / peak, 4),

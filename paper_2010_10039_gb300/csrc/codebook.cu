@@ -369,11 +369,26 @@ __device__ __forceinline__ void codebook_body(const CbArgs &g, uint8_t *arrays) 
     if (m >= 2) {
         // ---- bitonic sort of the keys (ascending: count, then id; unused last)
         if (small) {
-            // the exchange buffers are keys[0, 2P): every thread must be done
-            // reading them before the sorted keys go back to keys[0, P)
-            mykey = bitonic_sort_regs(mykey, P, A.keys);
+            // Sparse histograms: compact the used keys to threads 0..m-1 first
+            // (ranks by ballot), so only pow2_ceil(m) keys are sorted.
+            uint32_t Ps = P;
+            if (pow2_ceil(m) < P) {
+                Ps = pow2_ceil(m);
+                const bool u = mykey != ~0ull;
+                const uint32_t bal = __ballot_sync(0xFFFFFFFFu, u);
+                if (lane == 0) s_wsum[warp] = __popc(bal);
+                __syncthreads();
+                uint32_t r = __popc(bal & ((1u << lane) - 1));
+                for (uint32_t w = 0; w < warp; w++) r += s_wsum[w];
+                if (u) A.keys[r] = mykey;
+                __syncthreads();
+                mykey = tid < m ? A.keys[tid] : ~0ull;
+            }
+            // the exchange buffers are keys[0, 2Ps): every thread must be done
+            // reading them before the sorted keys go back to keys[0, Ps)
+            mykey = bitonic_sort_regs(mykey, Ps, A.keys);
             __syncthreads();
-            if (tid < P) A.keys[tid] = mykey;
+            if (tid < Ps) A.keys[tid] = mykey;
         } else {
             radix_sort_keys(g.hist, nbins, m, s_maxc, A.keys, P, s_rh, s_wsum);
         }
