@@ -97,34 +97,40 @@ __device__ __forceinline__ void decode_chunk(const DecArgs &a, const uint32_t *g
     Sym *out = reinterpret_cast<Sym *>(a.out);
     // Word indices are relative to the chunk's first word cw0 (32-bit: a chunk
     // spans far fewer than 2^32 words; lim stops reads at the stream's end).
-    // The buffer (hi:lo) holds the stream's bits [p, p + nb) MSB first, and wn
-    // is the next word to load, so p = 32 * (cw0 + wn) - nb at all times.
+    // The buffer (hi:lo) holds the stream's bits [p, p + nb) MSB first; nxt
+    // holds the word that follows them, already loaded, and wn is the word after
+    // nxt, so p = 32 * (cw0 + wn - 1) - nb at all times.  A refill splices nxt
+    // in and starts loading the next word, which is not needed before the next
+    // refill: the load's latency hides behind the symbols in between.
     const uint64_t cw0 = p0 >> 5;
     const uint32_t *cin = a.in + cw0;
     const uint64_t left = a.in_words > cw0 ? a.in_words - cw0 : 0;
     const uint32_t lim = left < 0xFFFFFFFFull ? (uint32_t)left : 0xFFFFFFFFu;
     auto word = [&](uint32_t k) { return k < lim ? __ldg(cin + k) : 0u; };
-    uint32_t hi, lo, nb, wn;
+    uint32_t hi, lo, nb, wn, nxt;
     auto start = [&](uint64_t p) {
         wn = (uint32_t)((p >> 5) - cw0);
         const uint32_t sh = p & 31, w0 = word(wn), w1 = word(wn + 1);
+        nxt = word(wn + 2);
         hi = __funnelshift_l(w1, w0, sh);
         lo = w1 << sh;
         nb = 64 - sh;
-        wn += 2;
+        wn += 3;
     };
-    auto pos = [&]() { return 32 * (cw0 + wn) - nb; };
+    auto pos = [&]() { return 32 * (cw0 + wn - 1) - nb; };
     start(p0);
     const uint32_t shL = 32 - L;
     // level-2 index: stream bits L..max_len-1 (used only when max_len - L <= kL2Bits)
     const uint32_t sh2 = 32 - (max_len <= 32 ? max_len : 32), m2 = max_len - L <= kL2Bits ? (1u << (max_len - L)) - 1 : 0u;
     bool ok = true;
     auto next = [&](uint32_t &s) {
-        // refill: the next word goes to buffer bits [nb, nb + 32) (predicated, no branch)
+        // refill: nxt goes to buffer bits [nb, nb + 32), then the following word
+        // is loaded into nxt (predicated, no branch)
         const bool need = nb <= 32;
-        const uint32_t w = need ? word(wn) : 0u;
+        const uint32_t w = need ? nxt : 0u;
         hi |= __funnelshift_rc(w, 0u, nb);
         lo |= __funnelshift_lc(0u, w, 32 - nb);
+        if (need) nxt = word(wn);
         wn += need;
         nb += need ? 32u : 0u;
         uint32_t e = dec_lut[hi >> shL];
