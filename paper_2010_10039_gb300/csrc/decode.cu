@@ -11,8 +11,10 @@
 //     by the next max_len - L bits, when they fit (at most kL2Bits bits and
 //     kL2Entries entries in all).
 // So a code costs one or two shared lookups; prefixes left at 0 continue the
-// First/Entry search from length L + 1 on the register buffer (First, Entry,
-// Count and, up to 4,096 symbols, sorted_syms in shared memory).  The stream
+// First/Entry search from length L + 1 on the register buffer (First, Entry
+// and Count in shared memory).  For alphabets of at most 1,024 symbols and
+// fields of few chunks, a pair table over the same windows gives two codes
+// per lookup when both fit in the window.  The stream
 // is read through a 64-bit register buffer refilled 32 bits at a time, and
 // decoded symbols are packed into 32-byte vector stores (one per
 // 32 / sizeof(sym) symbols), since neighbouring lanes write 2^M symbols apart.
@@ -24,7 +26,7 @@ namespace huff {
 
 constexpr int kDecThreads = 256;
 constexpr uint32_t kLutBits = 12;
-constexpr uint32_t kDecSmemSyms = 4096;     // sorted_syms copied to shared memory up to this alphabet
+constexpr uint32_t kDecPairBins = 1024;     // two-code table entries for alphabets up to this size
 constexpr uint32_t kDecInvalid = 0x8000u;   // table entry: no codeword starts with this window
 constexpr uint32_t kDecLong = 0x4000u;      // level-1 entry: prefix of longer codes, subtable index in bits 16..31
 constexpr uint32_t kL2Bits = 8;             // longest level-2 index
@@ -39,7 +41,7 @@ __shared__ uint32_t dec_lut[1u << kLutBits];
 __shared__ uint32_t dec_lut2[kL2Entries];
 __shared__ uint32_t dec_nlong[kDecThreads / 32 + 1];
 __shared__ uint16_t dec_lpfx[kL2Entries / 2];   // level-1 window of each numbered long prefix
-__shared__ uint32_t dec_syms[kDecSmemSyms];
+__shared__ uint32_t dec_pair[1u << kLutBits];
 
 struct DecArgs {
     const uint32_t *in;
@@ -53,6 +55,7 @@ struct DecArgs {
     uint8_t *out;
     uint32_t nbins;
     int vec_out;          // out is 16-byte aligned and a chunk is a whole number of 16-byte runs
+    int pair_out;         // out is 8-byte aligned and a chunk is a whole number of 8-byte runs
     uint32_t *status;
 };
 
@@ -73,14 +76,12 @@ __device__ __forceinline__ uint64_t window64(const uint32_t *in, uint64_t nwords
 // the window `win` of the stream at the code's start (valid for max_len bits).
 // Returns sym << 8 | len, or 0 when no codeword starts there.  Out of line:
 // only long codes come here.
-__device__ __noinline__ uint32_t decode_long(uint64_t win, uint32_t L, uint32_t max_len, const uint32_t *gsyms,
-                                             bool smem_syms) {
+__device__ __noinline__ uint32_t decode_long(uint64_t win, uint32_t L, uint32_t max_len, const uint32_t *gsyms) {
     for (uint32_t l = L + 1; l <= max_len; l++) {
         const uint64_t v = win >> (64 - l);
         if (v >= dec_first[l]) {
             if (v - dec_first[l] >= dec_count[l]) return 0;
-            const uint32_t k = dec_entry[l] + (uint32_t)(v - dec_first[l]);
-            return ((smem_syms ? dec_syms[k] : gsyms[k]) << 8) | l;
+            return (__ldg(gsyms + dec_entry[l] + (uint32_t)(v - dec_first[l])) << 8) | l;
         }
     }
     return 0;
@@ -91,7 +92,7 @@ __device__ __noinline__ uint32_t decode_long(uint64_t win, uint32_t L, uint32_t 
 // pend, through the status word.  Reads are bounded by the stream and writes
 // by the chunk, whatever the stream holds.
 template <int W>
-__device__ __forceinline__ void decode_chunk(const DecArgs &a, const uint32_t *gsyms, bool smem_syms, uint32_t L,
+__device__ __forceinline__ void decode_chunk(const DecArgs &a, const uint32_t *gsyms, bool pair, uint32_t L,
                                              uint32_t max_len, uint64_t i0, uint64_t i1, uint64_t p0, uint64_t pend) {
     using Sym = typename std::conditional<W == 1, uint8_t, typename std::conditional<W == 2, uint16_t, uint32_t>::type>::type;
     Sym *out = reinterpret_cast<Sym *>(a.out);
@@ -123,9 +124,9 @@ __device__ __forceinline__ void decode_chunk(const DecArgs &a, const uint32_t *g
     // level-2 index: stream bits L..max_len-1 (used only when max_len - L <= kL2Bits)
     const uint32_t sh2 = 32 - (max_len <= 32 ? max_len : 32), m2 = max_len - L <= kL2Bits ? (1u << (max_len - L)) - 1 : 0u;
     bool ok = true;
-    auto next = [&](uint32_t &s) {
-        // refill: nxt goes to buffer bits [nb, nb + 32), then the following word
-        // is loaded into nxt (predicated, no branch)
+    // refill: nxt goes to buffer bits [nb, nb + 32), then the following word
+    // is loaded into nxt (predicated, no branch)
+    auto refill = [&]() {
         const bool need = nb <= 32;
         const uint32_t w = need ? nxt : 0u;
         hi |= __funnelshift_rc(w, 0u, nb);
@@ -133,6 +134,9 @@ __device__ __forceinline__ void decode_chunk(const DecArgs &a, const uint32_t *g
         if (need) nxt = word(wn);
         wn += need;
         nb += need ? 32u : 0u;
+    };
+    // one code from a refilled buffer
+    auto single = [&](uint32_t &s) {
         uint32_t e = dec_lut[hi >> shL];
         if (e & kDecLong) e = dec_lut2[(e >> 16) * (m2 + 1) + ((hi >> sh2) & m2)];
         uint32_t l = e & 0xFFu;
@@ -143,7 +147,7 @@ __device__ __forceinline__ void decode_chunk(const DecArgs &a, const uint32_t *g
             uint32_t r = 0;
             if (e == 0) {
                 const uint64_t win = max_len <= nb ? ((uint64_t)hi << 32 | lo) : window64(a.in, a.in_words, pos());
-                r = decode_long(win, L, max_len, gsyms, smem_syms);
+                r = decode_long(win, L, max_len, gsyms);
             }
             if (r == 0) { ok = false; return; }
             s = r >> 8;
@@ -161,8 +165,55 @@ __device__ __forceinline__ void decode_chunk(const DecArgs &a, const uint32_t *g
         lo <<= l;
         nb -= l;
     };
+    auto next = [&](uint32_t &s) {
+        refill();
+        single(s);
+    };
     uint64_t i = i0;
-    if (a.vec_out) {
+    bool paired = false;
+    if constexpr (W <= 2) {
+    if (pair) {
+        paired = true;
+        // Two codes per lookup where a 12-bit window holds both (the pair table);
+        // symbols gather in a 64-bit register of 8 / W slots, written 8 bytes at
+        // a time (the chunk and the output are 8-byte aligned here).
+        constexpr uint32_t kSlots = 8 / W, kSymBits = 8 * W, kSymMask = W == 1 ? 0xFFu : 0xFFFFu;
+        uint64_t obuf = 0;
+        uint32_t oc = 0;
+        auto put = [&](uint32_t s) {
+            obuf |= (uint64_t)s << (kSymBits * oc);
+            if (++oc == kSlots) {
+                *reinterpret_cast<uint64_t *>(out + i) = obuf;
+                i += kSlots;
+                obuf = 0;
+                oc = 0;
+            }
+        };
+        while (i + oc < i1 && ok) {
+            refill();
+            const uint32_t e2 = dec_pair[hi >> shL];
+            uint32_t l1 = (e2 >> 20) & 15u;
+            if (l1 != 0) {
+                // take the second code only while the chunk still needs a symbol
+                const uint32_t l2 = i + oc + 1 < i1 ? (e2 >> 24) & 15u : 0u;
+                const uint32_t l = l1 + l2;          // at most 12
+                hi = __funnelshift_l(lo, hi, l);
+                lo <<= l;
+                nb -= l;
+                put(e2 & 0x3FFu);
+                if (l2) put((e2 >> 10) & 0x3FFu);
+            } else {
+                uint32_t sym = 0;
+                single(sym);
+                if (ok) put(sym);
+            }
+        }
+        // the last partial group
+        for (uint32_t k = 0; k < oc && ok; k++) out[i + k] = (Sym)((obuf >> (kSymBits * k)) & kSymMask);
+        if (ok) i += oc;
+    }
+    }
+    if (!paired && a.vec_out) {
         constexpr int kBatch = 32 / W;          // symbols per 32-byte store
         for (; i + kBatch <= i1 && ok; i += kBatch) {
             uint32_t r[8];
@@ -203,10 +254,6 @@ __global__ void __launch_bounds__(kDecThreads) decode_kernel(DecArgs a) {
         dec_entry[l] = hdr->entry[l];
         dec_count[l] = hdr->count[l];
     }
-    const uint32_t nused = hdr->nused;
-    const bool smem_syms = a.nbins <= kDecSmemSyms;
-    if (smem_syms)
-        for (uint32_t k = threadIdx.x; k < nused && k < kDecSmemSyms; k += blockDim.x) dec_syms[k] = sorted_syms[k];
     __syncthreads();
     // level 1 over L-bit windows: the decoding rule restricted to lengths <= L;
     // each thread takes 2^L / kDecThreads consecutive windows (at least one)
@@ -223,7 +270,7 @@ __global__ void __launch_bounds__(kDecThreads) decode_kernel(DecArgs a) {
             if (v >= dec_first[l]) {
                 if (v - dec_first[l] < dec_count[l]) {
                     const uint32_t k = dec_entry[l] + (uint32_t)(v - dec_first[l]);
-                    e = ((smem_syms ? dec_syms[k] : sorted_syms[k]) << 16) | l;
+                    e = (__ldg(sorted_syms + k) << 16) | l;
                 } else {
                     e = kDecInvalid;
                 }
@@ -268,7 +315,7 @@ __global__ void __launch_bounds__(kDecThreads) decode_kernel(DecArgs a) {
                 if (v >= dec_first[l]) {
                     if (v - dec_first[l] < dec_count[l]) {
                         const uint32_t k = dec_entry[l] + (uint32_t)(v - dec_first[l]);
-                        e = ((smem_syms ? dec_syms[k] : sorted_syms[k]) << 16) | l;
+                        e = (__ldg(sorted_syms + k) << 16) | l;
                     }
                     break;
                 }
@@ -277,11 +324,33 @@ __global__ void __launch_bounds__(kDecThreads) decode_kernel(DecArgs a) {
         }
         __syncthreads();
     }
+    // pair table over the same windows: s1 | s2 << 10 | len1 << 20 | len2 << 24
+    // when the window holds a first code of at most L bits (len2 = 0 when no
+    // second code fits in the rest of the window), 0 otherwise
+    const bool pair = a.nbins <= kDecPairBins && a.pair_out && W <= 2;
+    if (pair) {
+        for (uint32_t x = threadIdx.x; x < nwin; x += kDecThreads) {
+            const uint32_t e1 = dec_lut[x];
+            const uint32_t l1 = e1 & 0xFFu;
+            uint32_t e = 0;
+            if (l1 != 0) {
+                e = (e1 >> 16) | (l1 << 20);
+                // the rest of the window, shifted up; its low l1 bits are unknown,
+                // so a second code counts only if it lies within the known bits
+                const uint32_t x2 = (x << l1) & (nwin - 1);
+                const uint32_t f = dec_lut[x2];
+                const uint32_t l2 = f & 0xFFu;
+                if (l2 != 0 && l2 <= L - l1) e |= ((f >> 16) << 10) | (l2 << 24);
+            }
+            dec_pair[x] = e;
+        }
+        __syncthreads();
+    }
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; c < a.nchunks; c += stride) {
         const uint64_t i0 = c << a.chunk_log2;
         const uint64_t i1 = i0 + (1ull << a.chunk_log2) < a.n ? i0 + (1ull << a.chunk_log2) : a.n;
-        decode_chunk<W>(a, sorted_syms, smem_syms, L, max_len, i0, i1, a.offs[c], a.offs[c + 1]);
+        decode_chunk<W>(a, sorted_syms, pair, L, max_len, i0, i1, a.offs[c], a.offs[c + 1]);
     }
 }
 
@@ -301,6 +370,12 @@ huff_status decode_launch(const uint32_t *d_in, uint64_t total_bits, const uint6
     a.nbins = nbins;
     // 32-byte stores need a 16-byte aligned output and chunks of whole 16-byte runs
     a.vec_out = ((uintptr_t)d_out & 15) == 0 && ((1ull << chunk_log2) * (uint64_t)dtype) % 16 == 0;
+    // Two codes per lookup shorten each thread's serial chain, which is what
+    // bounds a field of few chunks (at most one CTA of chunks per SM); with
+    // more chunks the decode is issue-bound, and the one-code path's fixed
+    // 32-byte batches (no divergence, whole sectors) are faster.
+    a.pair_out = ((uintptr_t)d_out & 7) == 0 && ((1ull << chunk_log2) * (uint64_t)dtype) % 8 == 0 &&
+                 a.nchunks <= (uint64_t)sm_count() * kDecThreads;
     a.status = status;
     if (a.nchunks == 0) return HUFF_OK;
     void (*kern)(DecArgs) = dtype == HUFF_U8 ? decode_kernel<1> : dtype == HUFF_U16 ? decode_kernel<2> : decode_kernel<4>;
