@@ -135,6 +135,20 @@ def _hist_cases():
         fib.append(fib[-1] + fib[-2])
     cases.append(("fibonacci45", np.array(fib, dtype=np.uint32)))
     cases.append(("allzero", np.zeros(300, dtype=np.uint32)))
+    # boundaries of the codebook's paths: one id per thread (<= 1024 bins) or
+    # slices; shared arrays (<= 4096 bins) or global scratch
+    for nb in (1025, 4097):
+        cases.append((f"zipf{nb}", np.maximum(1, np.floor(3e6 * np.arange(1, nb + 1, dtype=np.float64) ** -1.1))
+                      .astype(np.uint32)[rng.permutation(nb)]))
+        cases.append((f"ties{nb}", rng.integers(0, 4, size=nb).astype(np.uint32)))
+    # counts of 2^24 and more: four radix passes over a large alphabet
+    big = rng.integers(1, 1000, size=8000).astype(np.uint32)
+    big[[5, 77, 4000]] = [1 << 30, (1 << 30) + 12345, 1 << 29]
+    cases.append(("bigcounts8000", big))
+    # a sparse histogram over a small alphabet: only pow2(m) keys are sorted
+    sp = np.zeros(1024, dtype=np.uint32)
+    sp[rng.choice(1024, size=3, replace=False)] = [7, 7, 2]
+    cases.append(("three_of_1024", sp))
     return cases
 
 
