@@ -181,9 +181,22 @@ huff_status huff_encode(const void *d_sym, uint64_t n, huff_dtype dtype, const v
 
 /*
  * Decode (Sec. IV-B2, treeless canonical decoding with First and Entry): one
- * thread per chunk walks the stream from d_chunk_bit_offset[c].
- *   d_out  n symbols of `dtype`
- * An invalid code records HUFF_ERR_INVALID_ARG.
+ * thread per chunk walks the stream from d_chunk_bit_offset[c] to
+ * d_chunk_bit_offset[c + 1] (the layout huff_encode writes).
+ *   d_in        stream words (uint32, MSB first), ceil(total_bits / 32) of them;
+ *               4-byte aligned
+ *   chunk_log2  M of the encode (2^M symbols per chunk), 0..30
+ *   d_codebook  the codebook the stream was encoded with (nbins must match)
+ *   d_out       n symbols of `dtype`, aligned to the element size; 8- or
+ *               16-byte alignment (with 2^M * sizeof(sym) a multiple of it)
+ *               enables wider stores
+ * Host-side argument errors return immediately.  On the device, a window
+ * that starts no codeword, or a chunk whose codes do not end exactly at the
+ * next chunk's offset, records HUFF_ERR_INVALID_ARG in the workspace status
+ * (huff_get_status); reads stay inside the stream and writes inside the
+ * chunk's n symbols whatever the stream holds, and a chunk stops at its
+ * first invalid code.  A corrupted stream that still parses into valid codes
+ * may decode to other symbols without an error.
  */
 huff_status huff_decode(const uint32_t *d_in, uint64_t total_bits, const uint64_t *d_chunk_bit_offset,
                         int chunk_log2, uint64_t n, huff_dtype dtype, const void *d_codebook,
