@@ -47,22 +47,27 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+def _bind(lib: ctypes.CDLL) -> ctypes.CDLL:
+    """Declares the C signatures on a loaded oracle library (the tests also
+    bind builds of deliberately altered copies of the source through this)."""
+    vp, u64, u32, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
+    lib.oracle_histogram.argtypes = [vp, u64, i32, u32, vp]
+    lib.oracle_lengths_two_queue.argtypes = [vp, u32, vp]
+    lib.oracle_lengths_heap.argtypes = [vp, u32, vp]
+    lib.oracle_canonical.argtypes = [vp, u32, vp, vp, vp, vp, vp, vp]
+    lib.oracle_encode.argtypes = [vp, u64, i32, vp, vp, u32, i32, vp, u64, vp, vp]
+    lib.oracle_decode.argtypes = [vp, u64, u64, vp, vp, vp, vp, u32, i32, vp]
+    for f in (lib.oracle_histogram, lib.oracle_lengths_two_queue, lib.oracle_lengths_heap,
+              lib.oracle_canonical, lib.oracle_encode, lib.oracle_decode):
+        f.restype = i32
+    return lib
+
+
 def _load():
     global _lib
     if _lib is None:
         build()
-        lib = ctypes.CDLL(_LIB)
-        vp, u64, u32, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
-        lib.oracle_histogram.argtypes = [vp, u64, i32, u32, vp]
-        lib.oracle_lengths_two_queue.argtypes = [vp, u32, vp]
-        lib.oracle_lengths_heap.argtypes = [vp, u32, vp]
-        lib.oracle_canonical.argtypes = [vp, u32, vp, vp, vp, vp, vp, vp]
-        lib.oracle_encode.argtypes = [vp, u64, i32, vp, vp, u32, i32, vp, u64, vp, vp]
-        lib.oracle_decode.argtypes = [vp, u64, u64, vp, vp, vp, vp, u32, i32, vp]
-        for f in (lib.oracle_histogram, lib.oracle_lengths_two_queue, lib.oracle_lengths_heap,
-                  lib.oracle_canonical, lib.oracle_encode, lib.oracle_decode):
-            f.restype = i32
-        _lib = lib
+        _lib = _bind(ctypes.CDLL(_LIB))
     return _lib
 
 

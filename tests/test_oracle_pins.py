@@ -257,6 +257,38 @@ def test_canonical_properties(kind):
     assert book["sorted_syms"].tolist() == order
 
 
+def _prefix_free_and_oriented(ln, code):
+    used = [s for s in range(len(ln)) if ln[s]]
+    bits = sorted(format(int(code[s]), f"0{int(ln[s])}b") for s in used)
+    for x, y in zip(bits, bits[1:]):
+        if y.startswith(x):
+            return False
+    byl = {}
+    for s in used:
+        byl.setdefault(int(ln[s]), []).append(int(code[s]))
+    lens = sorted(byl)
+    return all(max(byl[l2]) >> (l2 - l1) < min(byl[l1]) for i, l1 in enumerate(lens) for l2 in lens[i + 1:])
+
+
+def test_canonical_incomplete_lengths():
+    """Canonical codes from any length vector with Kraft sum <= 1 (not only
+    the complete ones Huffman gives) are prefix-free, in the orientation
+    Sec. IV-B2 asks for.  Example: lengths (1, 3, 3) have Kraft sum 3/4 and
+    give 1, 000, 001 (the rounding up in First matters here: 0, 000, 001
+    would not be prefix-free)."""
+    book = oracle.canonical(np.array([1, 3, 3], dtype=np.uint8))
+    assert [format(int(c), f"0{l}b") for c, l in zip(book["code"], [1, 3, 3])] == ["1", "000", "001"]
+    rng = np.random.default_rng(11)
+    for t in range(300):
+        n = int(rng.integers(1, 40))
+        ln = rng.integers(1, 12, size=n)
+        while (2.0 ** -ln.astype(np.float64)).sum() > 1.0:
+            ln[int(rng.integers(0, n))] += 1
+        ln = ln.astype(np.uint8)
+        book = oracle.canonical(ln)
+        assert _prefix_free_and_oriented(ln, book["code"]), ln.tolist()
+
+
 # ------------------------------------------------------------------ encode
 
 def _naive_bits(sym, book):
