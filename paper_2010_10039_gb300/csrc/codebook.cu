@@ -145,8 +145,12 @@ __device__ __forceinline__ void cp_segment(uint32_t len, uint32_t &begin, uint32
 }
 
 // Counts, then scans rh into first slots; totals[d] (d < ntotals) receives the
-// number of elements with digit d.  Ends with a barrier.
-template <typename Elem>
+// number of elements with digit d.  Ends with a barrier.  Counting needs no
+// ranks: ATOMIC counts with one shared atomic per element (on the 32-bit word
+// holding rh[digit][warp]; a count stays below 65,536, so nothing carries
+// into the neighbour), which beats the warp match when a step holds many
+// distinct digits; the match wins when they repeat.
+template <bool ATOMIC, typename Elem>
 __device__ void cpass_count(uint32_t len, Elem elem, uint16_t (*rh)[kRhStride], uint32_t *wsum, uint32_t *totals,
                             uint32_t ntotals) {
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -164,8 +168,13 @@ __device__ void cpass_count(uint32_t len, Elem elem, uint16_t (*rh)[kRhStride], 
         }
 #pragma unroll
         for (int q = 0; q < 4; q++) {
-            const uint32_t peers = __match_any_sync(0xFFFFFFFFu, e[q].valid ? e[q].digit : 0x10000u);
-            if (e[q].valid && __popc(peers & lt) == 0) rh[e[q].digit][warp] += (uint16_t)__popc(peers);
+            if (ATOMIC) {
+                if (e[q].valid)
+                    atomicAdd(reinterpret_cast<uint32_t *>(&rh[e[q].digit][warp & ~1u]), 1u << (16 * (warp & 1)));
+            } else {
+                const uint32_t peers = __match_any_sync(0xFFFFFFFFu, e[q].valid ? e[q].digit : 0x10000u);
+                if (e[q].valid && __popc(peers & lt) == 0) rh[e[q].digit][warp] += (uint16_t)__popc(peers);
+            }
         }
     }
     __syncthreads();
@@ -255,7 +264,9 @@ __device__ void radix_sort_keys(const uint32_t *hist, uint32_t nbins, uint32_t m
             return CpElem{true, (uint32_t)(key >> shift) & (kRadixDigits - 1), key};
         };
         const uint32_t len = pass == 0 ? nbins : m;
-        cpass_count(len, elem, rh, wsum, nullptr, 0);
+        // the low byte of varied counts spreads over many digits per step
+        if (pass == 0 && maxcount >= 256) cpass_count<true>(len, elem, rh, wsum, nullptr, 0);
+        else cpass_count<false>(len, elem, rh, wsum, nullptr, 0);
         cpass_scatter(len, elem, [&](uint32_t slot, uint64_t key) { dst[slot] = key; }, [](uint64_t) {}, rh);
     }
 }
@@ -574,7 +585,7 @@ __device__ __forceinline__ void codebook_body(const CbArgs &g, uint8_t *arrays) 
             const uint32_t l = A.lenS[i];
             return CpElem{l != 0, l, ((uint64_t)l << 32) | i};
         };
-        cpass_count(nbins, elem, s_rh, s_wsum, s_count, HUFF_MAX_LEN + 1);
+        cpass_count<false>(nbins, elem, s_rh, s_wsum, s_count, HUFF_MAX_LEN + 1);
         if (tid == 0) s_count[0] = 0;
         __syncthreads();
         first_entry();
