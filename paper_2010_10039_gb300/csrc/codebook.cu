@@ -585,7 +585,8 @@ __device__ __forceinline__ void codebook_body(const CbArgs &g, uint8_t *arrays) 
             const uint32_t l = A.lenS[i];
             return CpElem{l != 0, l, ((uint64_t)l << 32) | i};
         };
-        cpass_count<false>(nbins, elem, s_rh, s_wsum, s_count, HUFF_MAX_LEN + 1);
+        // (counting by atomics: a step of ids holds many lengths, 394 against 400 us at 65,536 bins)
+        cpass_count<true>(nbins, elem, s_rh, s_wsum, s_count, HUFF_MAX_LEN + 1);
         if (tid == 0) s_count[0] = 0;
         __syncthreads();
         first_entry();
