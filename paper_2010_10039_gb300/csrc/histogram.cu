@@ -98,8 +98,33 @@ __device__ __forceinline__ void count_one(uint32_t *h, uint32_t s, uint32_t mask
 template <typename Sym, bool PACKED, bool CARRY = false>
 __device__ __forceinline__ void count_vec(uint32_t *h, const uint4 &v, uint32_t mask, uint32_t &seen,
                                           const Carry &cy = Carry{nullptr, 0}, uint32_t *bad = nullptr) {
+    if (PACKED && CARRY) {
+        // all the vector's increments first, then the crossings: the increments
+        // do not wait for one another's results (a carry only has to land
+        // before the epoch's barrier)
+        constexpr int N = SymVec<Sym>::N;
+        uint32_t old[N], sh[N], sm[N];
 #pragma unroll
-    for (int j = 0; j < SymVec<Sym>::N; j++) count_one<PACKED, CARRY>(h, SymVec<Sym>::get(v, j), mask, seen, cy, bad);
+        for (int j = 0; j < N; j++) {
+            const uint32_t s = SymVec<Sym>::get(v, j);
+            seen |= s;
+            sm[j] = s & mask;
+            sh[j] = (sm[j] >> 15) << 4;
+            old[j] = atomicAdd(h + (s & (kPackedWords - 1)), 1u << sh[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < N; j++) {
+            if (((old[j] >> sh[j]) & 0xFFFFu) == 0x7FFFu) {
+                atomicSub(h + (sm[j] & (kPackedWords - 1)), 0x8000u << sh[j]);
+                if (sm[j] < cy.nbins) atomicAdd(cy.hist + sm[j], 0x8000u);
+                else *bad = 1;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < SymVec<Sym>::N; j++)
+            count_one<PACKED, CARRY>(h, SymVec<Sym>::get(v, j), mask, seen, cy, bad);
+    }
 }
 
 // Folds the shared-memory counts into the global histogram; counts in slots
