@@ -19,6 +19,9 @@
 namespace huff {
 
 constexpr int kHistThreads = 512;
+constexpr int kHistPackedThreads = 1024;      // the packed table fills one CTA per SM: give it more warps
+
+__host__ __device__ constexpr int hist_threads(bool packed) { return packed ? kHistPackedThreads : kHistThreads; }
 constexpr uint32_t kPackedWords = 32768;       // 65536 16-bit counters
 
 template <typename Sym>
@@ -157,7 +160,8 @@ __device__ void hist_flush(uint32_t *hsm, uint32_t *hist, uint32_t nbins, uint32
 }
 
 template <typename Sym, bool PACKED>
-__global__ void __launch_bounds__(kHistThreads, 2) hist_kernel(HistArgs a) {
+__global__ void __launch_bounds__(hist_threads(PACKED), PACKED ? 1 : 2) hist_kernel(HistArgs a) {
+    constexpr int T = hist_threads(PACKED);
     extern __shared__ __align__(16) uint32_t hsm[];
     const uint32_t words = PACKED ? kPackedWords : a.nrep * a.stride;
     const uint32_t mask = a.mask;
@@ -167,7 +171,7 @@ __global__ void __launch_bounds__(kHistThreads, 2) hist_kernel(HistArgs a) {
     uint32_t seen = 0, bad = 0;
 
     const uint4 *vec = reinterpret_cast<const uint4 *>(a.base + a.head * sizeof(Sym));
-    constexpr uint64_t kRound = 2ull * kHistThreads;              // vectors per CTA round
+    constexpr uint64_t kRound = 2ull * T;                         // vectors per CTA round
     constexpr uint32_t kSymsPerRound = kRound * SymVec<Sym>::N;
     // packed counters: a barrier at least every 32,768 symbols of the CTA (an
     // epoch), so that a counter at most 0x7FFF at its start stays below 0x10000
@@ -177,7 +181,7 @@ __global__ void __launch_bounds__(kHistThreads, 2) hist_kernel(HistArgs a) {
     const uint64_t nrounds = (a.nvec + kRound - 1) / kRound;
     uint32_t since = 0;
     for (uint64_t r = blockIdx.x; r < nrounds; r += gridDim.x) {
-        const uint64_t i0 = r * kRound + threadIdx.x, i1 = i0 + kHistThreads;
+        const uint64_t i0 = r * kRound + threadIdx.x, i1 = i0 + T;
         if (i1 < a.nvec) {
             uint4 v0 = vec[i0], v1 = vec[i1];
             count_vec<Sym, PACKED, PACKED>(my, v0, mask, seen, cy, &bad);
@@ -287,15 +291,16 @@ static huff_status launch_hist(const void *d_sym, uint64_t n, uint32_t nbins, ui
     void (*kern)(HistArgs) = packed ? hist_kernel<Sym, true> : hist_kernel<Sym, false>;
     if (!allow_dynamic_smem((const void *)kern, smem))
         return HUFF_ERR_CUDA;
+    const int threads = hist_threads(packed);
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kHistThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
     if (occ < 1) occ = 1;
-    uint64_t rounds = (a.nvec + 2 * kHistThreads - 1) / (2 * kHistThreads);
+    uint64_t rounds = (a.nvec + 2ull * threads - 1) / (2ull * threads);
     uint64_t grid = (uint64_t)sm_count() * occ;
     if (grid > rounds) grid = rounds;
     if (grid < 1) grid = 1;
     if (cudaMemsetAsync(d_hist, 0, nbins * sizeof(uint32_t), st) != cudaSuccess) return HUFF_ERR_CUDA;
-    kern<<<(unsigned)grid, kHistThreads, smem, st>>>(a);
+    kern<<<(unsigned)grid, threads, smem, st>>>(a);
     note_launch();
     return cudaGetLastError() == cudaSuccess ? HUFF_OK : HUFF_ERR_CUDA;
 }
