@@ -210,8 +210,8 @@ huff_status huff_decode(const uint32_t *d_in, uint64_t total_bits, const uint64_
  * cudaMalloc/cudaFree because they can synchronise the whole device.
  * Same arguments and output as huff_encode, except:
  *   - no d_ws: the encoder's scratch is a fixed device array inside the
- *     library (2 MiB + 64 bytes, held on every GPU that loads the library
- *     until the process exits);
+ *     library (2 MiB + 256 KiB + 256 bytes, held on every GPU that loads the
+ *     library until the process exits);
  *   - n may be at most 2^28 symbols (268,435,456); more returns
  *     HUFF_ERR_INVALID_ARG with nothing enqueued;
  *   - d_status: one caller-owned uint32 in device memory; the call sets it to

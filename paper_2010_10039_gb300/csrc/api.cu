@@ -104,7 +104,7 @@ uint64_t huff_max_output_words(uint64_t n, uint32_t max_len) {
 }
 
 size_t huff_workspace_bytes(uint64_t n, uint32_t nbins, const huff_params *p) {
-    size_t a = encode_scratch_bytes(n);
+    size_t a = encode_scratch_bytes(n, nbins);
     if (p && p->merge == HUFF_MERGE_SHUFFLE && p->chunk_log2 >= 4 && p->chunk_log2 <= 30) {
         const size_t b = shuffle_scratch_bytes(n, p->chunk_log2, p->reduce_log2);
         if (b > a) a = b;

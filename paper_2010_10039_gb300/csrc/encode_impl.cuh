@@ -64,6 +64,8 @@ struct EncArgs {
     uint64_t *desc;               // look-back descriptors by global tile id, zeroed before the launch
     int32_t reduce_log2;          // single launch: r, or -1 for the average-length rule
     uint32_t nsub_cap;            // at most this many sub-tiles per tile
+    const uint32_t *etab;         // single launch, codebook not in shared memory: the codebook's
+                                  // 32-bit entries in global memory (used when max_len <= 23)
 };
 
 template <typename Sym>
@@ -145,10 +147,14 @@ __device__ __forceinline__ uint64_t ent_code<uint64_t>(uint64_t e) { return e & 
 // slots (tmask + 1 >= nbins, slots past nbins have no codeword) and is indexed
 // with s & tmask; a symbol beyond the table is caught by the vector range test.
 // The global table (large alphabets) is read only for s < nbins.
-template <typename Entry, bool GTAB>
+template <typename Entry, int TAB>
 __device__ __forceinline__ Entry table_get(const Entry *tab, const uint64_t *gcw, uint32_t s, uint32_t nbins,
                                            uint32_t tmask) {
-    if (GTAB) {
+    if (TAB == 2) {
+        // the entries, precomputed in global memory
+        return s < nbins ? __ldg(tab + s) : entry_from_cw<Entry>(0ull);
+    } else if (TAB == 1) {
+        // converted from the codeword in global memory
         uint64_t c = s < nbins ? __ldg(gcw + s) : 0ull;
         return entry_from_cw<Entry>(c);
     } else {
@@ -446,7 +452,7 @@ struct EncShared {
 // Reduce-merge of one 16-byte vector: 2^R2 codewords per run, concatenated
 // in a 64-bit register.  FULL: all symbols valid and below nbins.  `bad`
 // collects kBad32 when a valid position has no codeword.
-template <typename Sym, typename Entry, bool GTAB, int R2, bool FULL>
+template <typename Sym, typename Entry, int TAB, int R2, bool FULL>
 __device__ __forceinline__ uint32_t merge_vec(const uint32_t *sv, uint32_t valid, const Entry *tab,
                                               const uint64_t *gcw, uint32_t nbins, uint32_t tmask, uint64_t *acc,
                                               uint32_t *rb, uint32_t &bad) {
@@ -462,7 +468,7 @@ __device__ __forceinline__ uint32_t merge_vec(const uint32_t *sv, uint32_t valid
 #pragma unroll
             for (int x = 0; x < RL; x++) {
                 const int xi = r * RL + x;
-                uint32_t en = (uint32_t)table_get<Entry, GTAB>(tab, gcw, sv[xi], nbins, tmask);
+                uint32_t en = (uint32_t)table_get<Entry, TAB>(tab, gcw, sv[xi], nbins, tmask);
                 if (!FULL && xi >= (int)valid) en = 0u;               // padding past n: length 0
                 bad |= en;
                 hi = __funnelshift_l(lo, hi, en);
@@ -477,7 +483,7 @@ __device__ __forceinline__ uint32_t merge_vec(const uint32_t *sv, uint32_t valid
 #pragma unroll
             for (int x = 0; x < RL; x++) {
                 const int xi = r * RL + x;
-                Entry en = table_get<Entry, GTAB>(tab, gcw, sv[xi], nbins, tmask);
+                Entry en = table_get<Entry, TAB>(tab, gcw, sv[xi], nbins, tmask);
                 if (!FULL && xi >= (int)valid) en = (Entry)0;        // padding past n: length 0
                 else bad |= en == 0 ? kBad32 : 0u;
                 const uint32_t l = ent_len<Entry>(en);
@@ -495,7 +501,7 @@ __device__ __forceinline__ uint32_t merge_vec(const uint32_t *sv, uint32_t valid
 // Places a run longer than 64 bits codeword by codeword (symbols from global
 // memory: the stage may be refilled already).  Kept out of line so the rare
 // path adds no registers or instructions to the placement loop.
-template <typename Sym, typename Entry, bool GTAB, uint32_t RMASK>
+template <typename Sym, typename Entry, int TAB, uint32_t RMASK>
 __device__ __noinline__ void place_long_run(uint32_t *ring, uint32_t base, uint32_t pos, const Sym *symp,
                                             uint64_t first, int count, uint64_t n, const Entry *tab,
                                             const uint64_t *gcw, uint32_t nbins, uint32_t tmask) {
@@ -504,7 +510,7 @@ __device__ __noinline__ void place_long_run(uint32_t *ring, uint32_t base, uint3
     for (int x = 0; x < count; x++) {
         const uint64_t i = first + x;
         if (i >= n) break;
-        Entry en = table_get<Entry, GTAB>(tab, gcw, (uint32_t)symp[i], nbins, tmask);
+        Entry en = table_get<Entry, TAB>(tab, gcw, (uint32_t)symp[i], nbins, tmask);
         const uint32_t l = ent_len<Entry>(en);
         if (l) sink.put64(ent_code<Entry>(en), l);
     }
@@ -524,7 +530,7 @@ __device__ __forceinline__ void load_table(Entry *tab, uint32_t tslots, const En
 // The 8 merge warps: reduce-merge every tile into the bit ring, publish its
 // aggregate and hand it to the look-back and write-out warps.  R2 = r:
 // 2^r codewords per register.
-template <typename Sym, typename Entry, bool GTAB, int R2, bool BATCH>
+template <typename Sym, typename Entry, int TAB, int R2, bool BATCH>
 __device__ void merge_warps(const EncArgs &a, const EncField *fields, const uint32_t *tbase, uint8_t *stage,
                             uint32_t *ring, Entry *tab, uint32_t total, uint32_t nsub1, uint32_t max_len1,
                             EncShared &S) {
@@ -581,7 +587,7 @@ __device__ void merge_warps(const EncArgs &a, const EncField *fields, const uint
         }
         if (f != cur_f) {
             // every merge thread is past its last lookup in the previous field's table
-            if (!GTAB) load_table<Entry>(tab, a.tslots, BATCH ? fields[f] : a.one);
+            if (TAB == 0) load_table<Entry>(tab, a.tslots, BATCH ? fields[f] : a.one);
             if (BATCH && tid == 0) S.mf = fields[f];
             cur_f = f;
             merge_sync();
@@ -631,8 +637,8 @@ __device__ void merge_warps(const EncArgs &a, const EncField *fields, const uint
                 if (full) {
                     const uint4 v = *reinterpret_cast<const uint4 *>(st + q * kEncVecBytes);
                     sym_from_vec(v, sv, Sym());
-                    if (!GTAB && vec_out_of_table(v, tmask, Sym())) bad |= kBad32;
-                    bits[k] = merge_vec<Sym, Entry, GTAB, R2, true>(sv, V, tab, gcw, nbins, tmask, acc[k], rb[k], bad);
+                    if (TAB == 0 && vec_out_of_table(v, tmask, Sym())) bad |= kBad32;
+                    bits[k] = merge_vec<Sym, Entry, TAB, R2, true>(sv, V, tab, gcw, nbins, tmask, acc[k], rb[k], bad);
                 } else {
                     const uint64_t i0 = s0 + (uint64_t)q * V;
                     const uint32_t vl = i0 >= n ? 0 : (n - i0 < V ? (uint32_t)(n - i0) : V);
@@ -641,7 +647,7 @@ __device__ void merge_warps(const EncArgs &a, const EncField *fields, const uint
 #pragma unroll
                     for (int x = 0; x < V; x++)
                         if (x < (int)vl && sv[x] > tmask) bad |= kBad32;
-                    bits[k] = merge_vec<Sym, Entry, GTAB, R2, false>(sv, vl, tab, gcw, nbins, tmask, acc[k], rb[k], bad);
+                    bits[k] = merge_vec<Sym, Entry, TAB, R2, false>(sv, vl, tab, gcw, nbins, tmask, acc[k], rb[k], bad);
                 }
             }
             if (bad & kBad32) {
@@ -713,7 +719,7 @@ __device__ void merge_warps(const EncArgs &a, const EncField *fields, const uint
                         if (bb) place_run<RMASK>(ring, base, pos, acc[k][r], bb);
                     } else {
                         // longer than the register (rare): codeword by codeword, out of line
-                        place_long_run<Sym, Entry, GTAB, RMASK>(ring, base, pos, symp,
+                        place_long_run<Sym, Entry, TAB, RMASK>(ring, base, pos, symp,
                                                                s0 + (uint64_t)q * V + r * RL, RL, n, tab, gcw,
                                                                nbins, tmask);
                     }
@@ -908,16 +914,16 @@ __host__ __device__ inline int enc_rule_r(uint64_t total_bits, uint64_t nsymbols
     return 4 - f;
 }
 
-template <typename Sym, typename Entry, bool GTAB, bool BATCH>
+template <typename Sym, typename Entry, int TAB, bool BATCH>
 __device__ void merge_dispatch(int r, const EncArgs &a, const EncField *fields, const uint32_t *tbase,
                                uint8_t *stage, uint32_t *ring, Entry *tab, uint32_t total, uint32_t nsub1,
                                uint32_t max_len1, EncShared &S) {
     switch (r) {
-        case 0: if constexpr (VecOf<Sym>::N <= 4) merge_warps<Sym, Entry, GTAB, 0, BATCH>(a, fields, tbase, stage, ring, tab, total, nsub1, max_len1, S); break;
-        case 1: if constexpr (VecOf<Sym>::N <= 4) merge_warps<Sym, Entry, GTAB, 1, BATCH>(a, fields, tbase, stage, ring, tab, total, nsub1, max_len1, S); break;
-        case 2: merge_warps<Sym, Entry, GTAB, 2, BATCH>(a, fields, tbase, stage, ring, tab, total, nsub1, max_len1, S); break;
-        case 3: if constexpr (VecOf<Sym>::N >= 8) merge_warps<Sym, Entry, GTAB, 3, BATCH>(a, fields, tbase, stage, ring, tab, total, nsub1, max_len1, S); break;
-        default: if constexpr (VecOf<Sym>::N >= 16) merge_warps<Sym, Entry, GTAB, 4, BATCH>(a, fields, tbase, stage, ring, tab, total, nsub1, max_len1, S); break;
+        case 0: if constexpr (VecOf<Sym>::N <= 4) merge_warps<Sym, Entry, TAB, 0, BATCH>(a, fields, tbase, stage, ring, tab, total, nsub1, max_len1, S); break;
+        case 1: if constexpr (VecOf<Sym>::N <= 4) merge_warps<Sym, Entry, TAB, 1, BATCH>(a, fields, tbase, stage, ring, tab, total, nsub1, max_len1, S); break;
+        case 2: merge_warps<Sym, Entry, TAB, 2, BATCH>(a, fields, tbase, stage, ring, tab, total, nsub1, max_len1, S); break;
+        case 3: if constexpr (VecOf<Sym>::N >= 8) merge_warps<Sym, Entry, TAB, 3, BATCH>(a, fields, tbase, stage, ring, tab, total, nsub1, max_len1, S); break;
+        default: if constexpr (VecOf<Sym>::N >= 16) merge_warps<Sym, Entry, TAB, 4, BATCH>(a, fields, tbase, stage, ring, tab, total, nsub1, max_len1, S); break;
     }
 }
 
@@ -995,11 +1001,26 @@ __global__ void __launch_bounds__(kEncCtaThreads, sizeof(Sym) == 1 ? 2 : 3) enco
         lookback_loop(a, fields, total, S);
         return;
     }
-    if (e32)
-        merge_dispatch<Sym, uint32_t, GTAB, BATCH>(r, a, fields, tbase, stage, ring, reinterpret_cast<uint32_t *>(tab),
-                                                   total, nsub1, max_len1, S);
-    else
-        merge_dispatch<Sym, uint64_t, GTAB, BATCH>(r, a, fields, tbase, stage, ring, tab, total, nsub1, max_len1, S);
+    // a codebook outside shared memory is read from a.etab (the 32-bit entries
+    // of a single field, TAB 2) or converted from its codewords (TAB 1)
+    constexpr int kTab = GTAB ? 1 : 0;
+    if (e32) {
+        bool done = false;
+        if constexpr (GTAB && !BATCH) {
+            if (a.etab) {
+                merge_dispatch<Sym, uint32_t, 2, BATCH>(r, a, fields, tbase, stage, ring, const_cast<uint32_t *>(a.etab),
+                                                        total, nsub1, max_len1, S);
+                done = true;
+            }
+        }
+        if (!done)
+            merge_dispatch<Sym, uint32_t, kTab, BATCH>(r, a, fields, tbase, stage, ring,
+                                                       GTAB ? nullptr : reinterpret_cast<uint32_t *>(tab), total, nsub1,
+                                                       max_len1, S);
+    } else {
+        merge_dispatch<Sym, uint64_t, kTab, BATCH>(r, a, fields, tbase, stage, ring, GTAB ? nullptr : tab, total, nsub1,
+                                                   max_len1, S);
+    }
 }
 
 }  // namespace huff

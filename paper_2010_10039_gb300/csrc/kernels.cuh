@@ -89,7 +89,7 @@ struct EncBatchConf {
 huff_status encode_launch(const void *d_sym, uint64_t n, huff_dtype dtype, const void *d_codebook, uint32_t nbins,
                           int chunk_log2, int reduce_log2, uint32_t *d_out, uint64_t cap, uint64_t *d_offs,
                           uint64_t *d_total, uint8_t *scratch, uint32_t *status, cudaStream_t st);
-size_t encode_scratch_bytes(uint64_t n);
+size_t encode_scratch_bytes(uint64_t n, uint32_t nbins);
 int encode_run_log2(huff_dtype dtype);
 // Symbols per sub-tile (the smallest tile) of a dtype.
 uint32_t encode_sub_symbols(huff_dtype dtype);

@@ -11,10 +11,13 @@
 
 namespace huff {
 
-// Largest input of one call, and the encoder scratch it needs (2 MiB + 64
-// bytes: a tile counter and a 16-byte descriptor per tile of >= 2048 symbols).
+// Largest input of one call, and the encoder scratch it needs: a tile counter
+// and a 16-byte descriptor per tile of >= 2048 symbols (2 MiB + 64 bytes,
+// rounded up to 256), then room for the 32-bit table entries of the largest
+// alphabet (256 KiB).
 constexpr uint64_t kNoAllocMaxSymbols = 1ull << 28;
-constexpr size_t kNoAllocScratchBytes = 64 + 16 * (kNoAllocMaxSymbols / 2048);
+constexpr size_t kNoAllocScratchBytes =
+    ((64 + 16 * (kNoAllocMaxSymbols / 2048) + 255) & ~size_t(255)) + 4ull * HUFF_MAX_BINS;
 
 // One copy per device that loads the library; it stays until the process exits.
 static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocScratchBytes];
@@ -75,7 +78,7 @@ extern "C" huff_status huff_encode_noalloc(const void *d_sym, uint64_t n, huff_d
         return HUFF_OK;
     }
     // the encoder clears the part of the scratch it uses before its launch
-    if (encode_scratch_bytes(n) > kNoAllocScratchBytes) return HUFF_ERR_INVALID_ARG;
+    if (encode_scratch_bytes(n, nbins) > kNoAllocScratchBytes) return HUFF_ERR_INVALID_ARG;
     return encode_launch(d_sym, n, dtype, d_codebook, nbins, prm.chunk_log2, prm.reduce_log2, d_out,
                          out_capacity_words, d_chunk_bit_offset, d_total_bits, scratch, d_status, st);
 }
