@@ -263,6 +263,32 @@ def test_hpc_field_full_size():
     _full_check(sym, 1024)
 
 
+@pytest.mark.parametrize("nbins", [5000, 20000])
+def test_long_codes_large_alphabet(nbins):
+    """Codes longer than 23 bits over an alphabet too large for the shared
+    table: the encoder reads 64-bit codewords from global memory (and the
+    32-bit entry table is not built)."""
+    import torch
+    fib = [1, 1]
+    while len(fib) < 44:
+        fib.append(fib[-1] + fib[-2])
+    h = np.ones(nbins, dtype=np.uint32)
+    h[:44] = fib
+    want = oracle.codebook(h)
+    assert want["max_len"] > 23
+    rng = np.random.default_rng(nbins)
+    sym = np.concatenate([np.arange(nbins, dtype=np.uint32),
+                          rng.integers(0, 48, size=100_000).astype(np.uint32)])
+    r = Run(sym, nbins)
+    r.codebook(torch.from_numpy(h.view(np.int32)).cuda()).encode()
+    assert r.status() == 0
+    _cmp_book(r.book_np(), want)
+    words, offs, tb = oracle.encode(sym, want, chunk_log2=10)
+    got, gtb = r.stream_np()
+    assert gtb == tb and np.array_equal(got, words)
+    assert np.array_equal(r.offs_np(), offs)
+
+
 @pytest.mark.parametrize("width", [2, 4])
 def test_packed_histogram_heavy_bins(width):
     """Alphabets above 16,384 bins count in packed 16-bit shared counters
