@@ -668,23 +668,59 @@ def run_batched(args, world, rank, local):
     torch.cuda.synchronize()
     ms_per_call = ev0.elapsed_time(ev1) / reps
 
-    # end to end: pinned host inputs in, encoded streams and offsets out, every step
+    # end to end: pinned host inputs in, encoded streams and offsets out, every
+    # step.  Two buffer sets, each with its own plan (the tuned settings), and
+    # a copy stream for each direction: step k + 1's inputs go in while step k
+    # encodes and its results come back.
     host_in = [f["sym"].cpu().pin_memory() for f in fields]
     host_out = [torch.empty_like(f["out"], device="cpu").pin_memory() for f in fields]
     host_off = [torch.empty_like(f["offsets"], device="cpu").pin_memory() for f in fields]
     nw = [(int(f["total_bits"].item()) + 31) // 32 for f in fields]
-    e2e_steps = max(1, min(K, 3))
+    fields2 = [{"sym": torch.empty_like(f["sym"]), "nbins": f["nbins"], "chunk_log2": f["chunk_log2"],
+                "out": torch.empty_like(f["out"]), "offsets": torch.empty_like(f["offsets"]),
+                "total_bits": torch.zeros_like(f["total_bits"])} for f in fields]
+    plan2 = huff.BatchPlan(fields2, autotune=False, reduce_log2=info["reduce_log2"],
+                           max_subtiles=info["max_subtiles"], ctas_per_sm=info["ctas_per_sm"])
+    sets = [(fields, plan), (fields2, plan2)]
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+    ev_in = [torch.cuda.Event(), torch.cuda.Event()]
+    ev_used = [torch.cuda.Event(), torch.cuda.Event()]
+    ev_read = [torch.cuda.Event(), torch.cuda.Event()]
+
+    def copy_in(b):
+        with torch.cuda.stream(s_in):
+            for f, h in zip(sets[b][0], host_in):
+                f["sym"].copy_(h, non_blocking=True)
+            ev_in[b].record(s_in)
+
+    e2e_steps = max(2, min(K, 4))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        for f, h in zip(fields, host_in):
-            f["sym"].copy_(h, non_blocking=True)
-        plan.encode()
-        for f, ho, hf, w in zip(fields, host_out, host_off, nw):
-            ho[:w].copy_(f["out"][:w], non_blocking=True)
-            hf.copy_(f["offsets"], non_blocking=True)
-        torch.cuda.synchronize()
+    copy_in(0)
+    for k in range(e2e_steps):
+        b = k % 2
+        if k + 1 < e2e_steps:
+            if k >= 1:
+                s_in.wait_event(ev_used[1 - b])          # step k - 1 no longer reads those inputs
+            copy_in(1 - b)
+        stream.wait_event(ev_in[b])
+        if k >= 2:
+            stream.wait_event(ev_read[b])                # step k - 2's results are off the device
+        sets[b][1].encode()
+        ev_used[b].record(stream)
+        with torch.cuda.stream(s_out):
+            s_out.wait_event(ev_used[b])
+            for f, ho, hf, w in zip(sets[b][0], host_out, host_off, nw):
+                ho[:w].copy_(f["out"][:w], non_blocking=True)
+                hf.copy_(f["offsets"], non_blocking=True)
+            ev_read[b].record(s_out)
+    torch.cuda.synchronize()
     e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world)
+    for fs, pl in sets:
+        st = pl.status()
+        if any(st):
+            raise RuntimeError(f"end-to-end run: device status {[huff.STATUS.get(x, x) for x in st if x][:4]}")
+    del plan2, fields2
 
     if rank != 0:
         return
