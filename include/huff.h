@@ -214,15 +214,20 @@ huff_status huff_decode(const uint32_t *d_in, uint64_t total_bits, const uint64_
  *     library until the process exits);
  *   - n may be at most 2^28 symbols (268,435,456); more returns
  *     HUFF_ERR_INVALID_ARG with nothing enqueued;
+ *   - p->merge must be HUFF_MERGE_AUTO or HUFF_MERGE_SCAN (the paper-layout
+ *     merge needs chunk slots the fixed array does not hold): any other
+ *     value returns HUFF_ERR_INVALID_ARG;
  *   - d_status: one caller-owned uint32 in device memory; the call sets it to
  *     0 and the kernel records the first device error there (huff_status
  *     codes), which the caller reads after synchronising.
- * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  Every call uses the same array and clears what it needs first, so
- * calls that overlap on the GPU (other streams, other host threads) race and
- * must be serialised by the caller.  No cudaMalloc, cudaFree or allocating
- * library routine is called.
+ * The array's device address is looked up on every call made outside a
+ * stream capture (so calls after a cudaDeviceReset use the new context's
+ * array); a call inside a capture reuses the address of the last uncaptured
+ * call on the same device, so the first call on a device must come before
+ * any capture (else HUFF_ERR_INVALID_ARG).  Every call uses the same array
+ * and clears what it needs first, so calls that overlap on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * No cudaMalloc, cudaFree or allocating library routine is called.
  */
 huff_status huff_encode_noalloc(const void *d_sym, uint64_t n, huff_dtype dtype, const void *d_codebook,
                                 uint32_t nbins, const huff_params *p, uint32_t *d_out, uint64_t out_capacity_words,

@@ -26,21 +26,34 @@ constexpr int kMaxDevices = 64;
 static uint8_t *g_scratch_addr[kMaxDevices];
 static std::mutex g_scratch_mu;
 
-// Device address of the array on the current device (looked up once per device).
-static uint8_t *noalloc_scratch(huff_status *err) {
+// Device address of the array on the current device.  Outside a stream
+// capture it is looked up on every call, so a call after cudaDeviceReset (a
+// new primary context, the module loaded again) gets the new address.  While
+// `st` is being captured no lookup is made -- it could load the module inside
+// the capture -- and the address of the last uncaptured call on this device
+// is used; the first call on a device must therefore come before any capture.
+static uint8_t *noalloc_scratch(cudaStream_t st, huff_status *err) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         *err = HUFF_ERR_CUDA;
         return nullptr;
     }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        *err = HUFF_ERR_CUDA;
+        return nullptr;
+    }
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
+    if (cs == cudaStreamCaptureStatusNone) {
         void *ptr = nullptr;
         if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
             *err = HUFF_ERR_CUDA;
             return nullptr;
         }
         g_scratch_addr[dev] = static_cast<uint8_t *>(ptr);
+    } else if (!g_scratch_addr[dev]) {
+        *err = HUFF_ERR_INVALID_ARG;          // first call on this device inside a capture
+        return nullptr;
     }
     return g_scratch_addr[dev];
 }
@@ -67,10 +80,13 @@ extern "C" huff_status huff_encode_noalloc(const void *d_sym, uint64_t n, huff_d
         return HUFF_ERR_INVALID_ARG;
     if (prm.chunk_log2 < 4 || prm.chunk_log2 > 30 || prm.chunk_log2 < encode_run_log2(dtype)) return HUFF_ERR_INVALID_ARG;
     if (prm.reduce_log2 != -1 && (prm.reduce_log2 < 0 || prm.reduce_log2 > prm.chunk_log2)) return HUFF_ERR_INVALID_ARG;
-    huff_status err = HUFF_OK;
-    uint8_t *scratch = noalloc_scratch(&err);
-    if (!scratch) return err;
+    // the fixed array is sized for the fused encoder only: the paper-layout
+    // merge (HUFF_MERGE_SHUFFLE) needs chunk slots it does not have
+    if (prm.merge != HUFF_MERGE_AUTO && prm.merge != HUFF_MERGE_SCAN) return HUFF_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
+    huff_status err = HUFF_OK;
+    uint8_t *scratch = noalloc_scratch(st, &err);
+    if (!scratch) return err;
     if (cudaMemsetAsync(d_status, 0, sizeof(uint32_t), st) != cudaSuccess) return HUFF_ERR_CUDA;
     if (n == 0) {
         if (cudaMemsetAsync(d_chunk_bit_offset, 0, 8, st) != cudaSuccess) return HUFF_ERR_CUDA;
