@@ -92,7 +92,11 @@ typedef struct {
 typedef struct {
     int32_t chunk_log2;    /* M: one chunk offset per 2^M symbols; 4..30; paper default 10     */
     int32_t reduce_log2;   /* r: 2^r consecutive symbols merged per thread in registers;
-                              -1 = pick r from the average codeword length (Sec. IV-C rule)   */
+                              -1 = pick r from the average codeword length (Sec. IV-C rule,
+                              as huff_reduce_factor with 32-bit words).  Whatever r is asked
+                              for or ruled, the scan encoder then clamps it to what its
+                              registers allow: [2, 4] for u8, [2, 3] for u16, [0, 2] for u32;
+                              the shuffle encoder takes r as given (<= 4; -1 = 3, fixed)      */
     int32_t block_threads; /* reserved: the encoders' CTA shapes are fixed per dtype (the
                               autotuner of the batched form picks CTAs per SM); any value is
                               accepted and ignored                                            */
@@ -115,7 +119,9 @@ void huff_default_params(huff_params *p);
 
 /*
  * Reduction factor rule of Sec. IV-C: floor(log2 beta) + r + 1 = log2(word_bits),
- * clamped to [1, 5]; beta = average codeword length in bits.
+ * solved for r and clamped to [0, log2(word_bits)]; beta = average codeword
+ * length in bits (> 0, else 3 is returned).  This is the rule's value; the
+ * encoders' own clamps (see huff_params.reduce_log2) apply after it.
  */
 int huff_reduce_factor(double avg_bits, int word_bits);
 
@@ -233,6 +239,21 @@ huff_status huff_encode_noalloc(const void *d_sym, uint64_t n, huff_dtype dtype,
                                 uint32_t nbins, const huff_params *p, uint32_t *d_out, uint64_t out_capacity_words,
                                 uint64_t *d_chunk_bit_offset, uint64_t *d_total_bits, uint32_t *d_status,
                                 void *stream);
+
+/* Failure-detection test hook (no paper counterpart): huff_encode with the
+ * default parameters, except that the encoder's tile ids start at 1, so tile 0
+ * is never encoded and never publishes its descriptor, and the decoupled
+ * look-back (Sec. IV-B's prefix sum done in one pass) gives up after
+ * `poll_limit` polls (1..2^22) instead of the default 2^22.  The look-back of
+ * tile 1 therefore must give up: the launch still completes, the workspace
+ * status reads HUFF_ERR_TIMEOUT, and the output stream is invalid (writes stay
+ * within out_capacity_words).  Requires n above eight encode sub-tiles (the
+ * largest tile), so that there is a tile 1; else HUFF_ERR_INVALID_ARG.  Arguments as in
+ * huff_encode.  For tests of the bounded waits only. */
+huff_status huff_encode_fault_test(const void *d_sym, uint64_t n, huff_dtype dtype, const void *d_codebook,
+                                   uint32_t nbins, uint32_t *d_out, uint64_t out_capacity_words,
+                                   uint64_t *d_chunk_bit_offset, uint64_t *d_total_bits, uint32_t poll_limit,
+                                   void *d_ws, void *stream);
 
 /* ------------------------------------------------------------------------
  * Batched encoding.  The paper encodes one field per call; the batch form

@@ -109,6 +109,7 @@ def lib() -> ctypes.CDLL:
             "huff_encode": (i32, [vp, u64, i32, vp, u32, P, vp, u64, vp, vp, vp, vp]),
             "huff_decode": (i32, [vp, u64, vp, i32, u64, i32, vp, u32, vp, vp, vp]),
             "huff_encode_noalloc": (i32, [vp, u64, i32, vp, u32, P, vp, u64, vp, vp, vp, vp]),
+            "huff_encode_fault_test": (i32, [vp, u64, i32, vp, u32, vp, u64, vp, vp, u32, vp, vp]),
             "huff_get_status": (i32, [vp, vp]),
             "huff_status_string": (ctypes.c_char_p, [i32]),
             "huff_launch_count": (u64, []),
@@ -248,6 +249,16 @@ def huff_encode_noalloc(sym, codebook, nbins: int, out, offsets, total_bits, sta
     _check(lib().huff_encode_noalloc(_ptr(sym), n, dt, _ptr(codebook), nbins, ctypes.byref(p), _ptr(out), cap,
                                      _ptr(offsets), _ptr(total_bits), _ptr(status), _stream(stream)),
            "huff_encode_noalloc")
+
+
+def huff_encode_fault_test(sym, codebook, nbins: int, out, offsets, total_bits, ws, poll_limit: int,
+                           stream=None) -> None:
+    """Failure-detection hook: an encode whose tile 0 is never encoded and
+    whose look-back gives up after `poll_limit` polls; the workspace status
+    then reads HUFF_ERR_TIMEOUT."""
+    _check(lib().huff_encode_fault_test(_ptr(sym), sym.numel(), dtype_code(sym), _ptr(codebook), nbins, _ptr(out),
+                                        out.numel(), _ptr(offsets), _ptr(total_bits), poll_limit, _ptr(ws),
+                                        _stream(stream)), "huff_encode_fault_test")
 
 
 def huff_decode(stream_words, total_bits: int, offsets, chunk_log2: int, n: int, dtype: int, codebook, nbins: int,

@@ -90,8 +90,8 @@ int huff_reduce_factor(double avg_bits, int word_bits) {
     if (!(avg_bits > 0) || word_bits <= 0) return 3;
     int lw = (int)std::lround(std::log2((double)word_bits));
     int r = lw - 1 - (int)std::floor(std::log2(avg_bits));
-    if (r < 1) r = 1;
-    if (r > 5) r = 5;
+    if (r < 0) r = 0;
+    if (r > lw) r = lw;
     return r;
 }
 
@@ -161,6 +161,24 @@ huff_status huff_encode(const void *d_sym, uint64_t n, huff_dtype dtype, const v
                                      status_of(d_ws), st);
     return encode_launch(d_sym, n, dtype, d_codebook, nbins, prm.chunk_log2, prm.reduce_log2, d_out, out_capacity_words,
                          d_chunk_bit_offset, d_total_bits, scratch_of(d_ws), status_of(d_ws), st);
+}
+
+huff_status huff_encode_fault_test(const void *d_sym, uint64_t n, huff_dtype dtype, const void *d_codebook,
+                                   uint32_t nbins, uint32_t *d_out, uint64_t out_capacity_words,
+                                   uint64_t *d_chunk_bit_offset, uint64_t *d_total_bits, uint32_t poll_limit,
+                                   void *d_ws, void *stream) {
+    if (!dtype_ok(dtype) || !nbins_ok(dtype, nbins) || !d_codebook || !d_chunk_bit_offset || !d_total_bits ||
+        !d_ws || !d_sym || !d_out || n >= (1ull << 32) || n <= encode_sub_symbols(dtype) * 8ull)   // an encode tile holds at most 8 sub-tiles
+        return HUFF_ERR_INVALID_ARG;
+    if (poll_limit < 1 || poll_limit > kSpinLimit) return HUFF_ERR_INVALID_ARG;
+    if (((uintptr_t)d_codebook & 15) != 0 || !elem_aligned(d_sym, dtype) || ((uintptr_t)d_out & 3) != 0 ||
+        ((uintptr_t)d_chunk_bit_offset & 7) != 0 || ((uintptr_t)d_total_bits & 7) != 0)
+        return HUFF_ERR_INVALID_ARG;
+    huff_params prm;
+    huff_default_params(&prm);
+    return encode_launch_ex(d_sym, n, dtype, d_codebook, nbins, prm.chunk_log2, prm.reduce_log2, d_out,
+                            out_capacity_words, d_chunk_bit_offset, d_total_bits, scratch_of(d_ws), status_of(d_ws),
+                            (cudaStream_t)stream, 1u, poll_limit);
 }
 
 huff_status huff_decode(const uint32_t *d_in, uint64_t total_bits, const uint64_t *d_chunk_bit_offset,

@@ -41,7 +41,8 @@ static uint32_t pow2_at_least(uint32_t x) {
 template <typename Sym>
 static huff_status launch_encode(const void *d_sym, uint64_t n, const void *d_codebook, uint32_t nbins_host,
                                  int chunk_log2, int reduce_log2, uint32_t *d_out, uint64_t cap, uint64_t *d_offs,
-                                 uint64_t *d_total, uint8_t *scratch, uint32_t *status, cudaStream_t st) {
+                                 uint64_t *d_total, uint8_t *scratch, uint32_t *status, cudaStream_t st,
+                                 uint32_t id_offset, uint32_t spin_limit) {
     constexpr uint32_t SUB = enc_sub_syms<Sym>();
     EncArgs a{};
     a.one.sym = static_cast<const uint8_t *>(d_sym);
@@ -64,6 +65,8 @@ static huff_status launch_encode(const void *d_sym, uint64_t n, const void *d_co
     a.desc = reinterpret_cast<uint64_t *>(scratch + 64);
     a.reduce_log2 = reduce_log2;
     a.nsub_cap = kEncMaxSubs;
+    a.id_offset = id_offset;
+    a.spin_limit = spin_limit;
     const uint64_t max_tiles = (n + SUB - 1) / SUB;
     if (cudaMemsetAsync(scratch, 0, 64 + 16 * max_tiles, st) != cudaSuccess) return HUFF_ERR_CUDA;
     const bool gtab = nbins_host > kEncSmemTableBins;
@@ -87,15 +90,23 @@ static huff_status launch_encode(const void *d_sym, uint64_t n, const void *d_co
     return cudaGetLastError() == cudaSuccess ? HUFF_OK : HUFF_ERR_CUDA;
 }
 
+huff_status encode_launch_ex(const void *d_sym, uint64_t n, huff_dtype dtype, const void *d_codebook, uint32_t nbins,
+                             int chunk_log2, int reduce_log2, uint32_t *d_out, uint64_t cap, uint64_t *d_offs,
+                             uint64_t *d_total, uint8_t *scratch, uint32_t *status, cudaStream_t st, uint32_t id_offset,
+                             uint32_t spin_limit) {
+    switch (dtype) {
+        case HUFF_U8: return launch_encode<uint8_t>(d_sym, n, d_codebook, nbins, chunk_log2, reduce_log2, d_out, cap, d_offs, d_total, scratch, status, st, id_offset, spin_limit);
+        case HUFF_U16: return launch_encode<uint16_t>(d_sym, n, d_codebook, nbins, chunk_log2, reduce_log2, d_out, cap, d_offs, d_total, scratch, status, st, id_offset, spin_limit);
+        case HUFF_U32: return launch_encode<uint32_t>(d_sym, n, d_codebook, nbins, chunk_log2, reduce_log2, d_out, cap, d_offs, d_total, scratch, status, st, id_offset, spin_limit);
+    }
+    return HUFF_ERR_INVALID_ARG;
+}
+
 huff_status encode_launch(const void *d_sym, uint64_t n, huff_dtype dtype, const void *d_codebook, uint32_t nbins,
                           int chunk_log2, int reduce_log2, uint32_t *d_out, uint64_t cap, uint64_t *d_offs,
                           uint64_t *d_total, uint8_t *scratch, uint32_t *status, cudaStream_t st) {
-    switch (dtype) {
-        case HUFF_U8: return launch_encode<uint8_t>(d_sym, n, d_codebook, nbins, chunk_log2, reduce_log2, d_out, cap, d_offs, d_total, scratch, status, st);
-        case HUFF_U16: return launch_encode<uint16_t>(d_sym, n, d_codebook, nbins, chunk_log2, reduce_log2, d_out, cap, d_offs, d_total, scratch, status, st);
-        case HUFF_U32: return launch_encode<uint32_t>(d_sym, n, d_codebook, nbins, chunk_log2, reduce_log2, d_out, cap, d_offs, d_total, scratch, status, st);
-    }
-    return HUFF_ERR_INVALID_ARG;
+    return encode_launch_ex(d_sym, n, dtype, d_codebook, nbins, chunk_log2, reduce_log2, d_out, cap, d_offs, d_total,
+                            scratch, status, st, 0u, 0u);
 }
 
 uint32_t encode_sub_symbols(huff_dtype dtype) {

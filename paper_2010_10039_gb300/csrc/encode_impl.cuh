@@ -66,7 +66,13 @@ struct EncArgs {
     uint32_t nsub_cap;            // at most this many sub-tiles per tile
     const uint32_t *etab;         // single launch, codebook not in shared memory: the codebook's
                                   // 32-bit entries in global memory (used when max_len <= 23)
+    uint32_t id_offset;           // added to every tile id taken (0; the failure-detection test
+                                  // passes 1, so tile 0 is never encoded)
+    uint32_t spin_limit;          // look-back polls before giving up (0: kSpinLimit)
 };
+
+// Tile id taken from the launch's counter.
+__device__ __forceinline__ uint32_t take_tile(const EncArgs &a) { return atomicAdd(a.tile_counter, 1u) + a.id_offset; }
 
 template <typename Sym>
 struct VecOf {
@@ -257,8 +263,11 @@ __device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t *p) {
 // Decoupled look-back by one warp, 128 predecessor descriptors per step:
 // returns the exclusive stream offset of tile j (length L) of a field whose
 // descriptors start at desc and, in lane 0, the previous tile's last 32 bits;
-// publishes tile j's inclusive offset.
-static __device__ uint64_t lookback_warp(uint64_t *desc, uint32_t *status, uint64_t j, uint64_t L, uint32_t *prev_tail) {
+// publishes tile j's inclusive offset.  A tile that has not published after
+// spin_limit polls records HUFF_ERR_TIMEOUT and the look-back goes on with
+// what it has (the stream is then invalid, but the launch completes).
+static __device__ uint64_t lookback_warp(uint64_t *desc, uint32_t *status, uint64_t j, uint64_t L, uint32_t *prev_tail,
+                                         uint32_t spin_limit) {
     const uint32_t lane = threadIdx.x & 31;
     uint64_t excl = 0;
     int64_t base = (int64_t)j;                 // look at tiles [base-128, base)
@@ -281,7 +290,7 @@ static __device__ uint64_t lookback_warp(uint64_t *desc, uint32_t *status, uint6
             znear = min(znear, __shfl_xor_sync(0xFFFFFFFFu, znear, o));
         }
         if (znear < pnear) {                   // a closer tile has not published yet
-            if (++spins > kSpinLimit) {
+            if (++spins > spin_limit) {
                 if (lane == 0) set_error(status, HUFF_ERR_TIMEOUT);
                 break;
             }
@@ -303,7 +312,7 @@ static __device__ uint64_t lookback_warp(uint64_t *desc, uint32_t *status, uint6
         st_relaxed_u64(&desc[2 * j + 1], kFlagPre | (excl + L));
         // the previous tile's last 32 bits travel in its aggregate word
         uint64_t agg = 0;
-        for (uint32_t sp = 0; sp < kSpinLimit; sp++) {
+        for (uint32_t sp = 0; sp < spin_limit; sp++) {
             agg = ld_relaxed_u64(&desc[2 * (j - 1)]);
             if (agg) break;
         }
@@ -349,7 +358,7 @@ __device__ __forceinline__ void produce_next(const EncArgs &a, const EncField *f
     constexpr uint32_t SUB = enc_sub_syms<Sym>();
     if (p.sub >= p.nsub && p.tile < total) {
         p.tile = p.next;
-        if (p.tile < total) p.next = atomicAdd(a.tile_counter, 1u);   // predicated: not waited on here
+        if (p.tile < total) p.next = take_tile(a);   // predicated: not waited on here
         p.sub = 0;
         if (p.tile < total) {
             p.f = BATCH ? field_of(tbase, a.nfields, p.tile) : 0u;
@@ -394,7 +403,7 @@ __device__ __forceinline__ void produce_next_one(const EncArgs &a, ProducerOne &
         p.tile = p.next;
         // predicated, not selected: nothing reads the new id before the next
         // tile switch, so the atomic's round trip does not stall the warp
-        if (p.tile < total) p.next = atomicAdd(a.tile_counter, 1u);
+        if (p.tile < total) p.next = take_tile(a);
         p.sub = 0;
     }
     const int s = (int)(p.slot % kEncStages);
@@ -559,9 +568,9 @@ __device__ void merge_warps(const EncArgs &a, const EncField *fields, const uint
             prod.nsub = 0;
             prod.tile = 0;
             prod.f = 0;
-            prod.next = atomicAdd(a.tile_counter, 1u);
+            prod.next = take_tile(a);
         } else {
-            one.next = atomicAdd(a.tile_counter, 1u);
+            one.next = take_tile(a);
             for (int i = 0; i < kEncStages; i++) stage_field[i] = 0;
         }
         for (int i = 0; i < kEncStages; i++) {
@@ -770,7 +779,8 @@ static __device__ void lookback_loop(const EncArgs &a, const EncField *fields, u
             const uint32_t L = S.slot[sl].L;
             uint64_t G = 0;
             uint32_t prev = 0;
-            if (j > 0) G = lookback_warp(a.desc + 2 * (uint64_t)F.tile_base, F.status, j, L, &prev);
+            if (j > 0) G = lookback_warp(a.desc + 2 * (uint64_t)F.tile_base, F.status, j, L, &prev,
+                                         a.spin_limit ? a.spin_limit : kSpinLimit);
             if (lane == 0) {
                 S.slot[sl].G = G;
                 S.slot[sl].prev = prev;
@@ -905,13 +915,14 @@ __host__ __device__ inline int enc_clamp_r(int r) {
 }
 
 // Reduction factor rule of Sec. IV-C: floor(log2 beta) + r + 1 = log2(32),
-// beta = total_bits / nsymbols the average codeword length.
+// beta = total_bits / nsymbols the average codeword length, clamped to
+// [0, 5] like huff_reduce_factor (the caller then applies the register clamp).
 __host__ __device__ inline int enc_rule_r(uint64_t total_bits, uint64_t nsymbols) {
     // floor(log2(beta)): largest f with nsymbols * 2^f <= total_bits
     int f = 0;
     while (f < 62 && nsymbols && (nsymbols << (f + 1)) <= total_bits && ((nsymbols << (f + 1)) >> (f + 1)) == nsymbols)
         f++;
-    return 4 - f;
+    return f > 4 ? 0 : 4 - f;
 }
 
 template <typename Sym, typename Entry, int TAB, bool BATCH>

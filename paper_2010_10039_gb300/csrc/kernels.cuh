@@ -89,6 +89,14 @@ struct EncBatchConf {
 huff_status encode_launch(const void *d_sym, uint64_t n, huff_dtype dtype, const void *d_codebook, uint32_t nbins,
                           int chunk_log2, int reduce_log2, uint32_t *d_out, uint64_t cap, uint64_t *d_offs,
                           uint64_t *d_total, uint8_t *scratch, uint32_t *status, cudaStream_t st);
+// The same with two failure-detection knobs: id_offset is added to every tile
+// id the encoder takes (1 leaves tile 0 unencoded, so the look-back of tile 1
+// can only give up), and spin_limit bounds the look-back's polls (0: the
+// default limit).
+huff_status encode_launch_ex(const void *d_sym, uint64_t n, huff_dtype dtype, const void *d_codebook, uint32_t nbins,
+                             int chunk_log2, int reduce_log2, uint32_t *d_out, uint64_t cap, uint64_t *d_offs,
+                             uint64_t *d_total, uint8_t *scratch, uint32_t *status, cudaStream_t st, uint32_t id_offset,
+                             uint32_t spin_limit);
 size_t encode_scratch_bytes(uint64_t n, uint32_t nbins);
 int encode_run_log2(huff_dtype dtype);
 // Symbols per sub-tile (the smallest tile) of a dtype.

@@ -45,7 +45,7 @@ def test_codebook_layout_sizes(lib):
 
 def test_reduce_factor_rule(lib):
     """Sec. IV-C: floor(log2 beta) + r + 1 = log2(32): beta 1.03 -> 4, 2.73 -> 3,
-    4.1 -> 2, 8.3 -> 1 (clamped to [1, 5])."""
+    4.1 -> 2, 8.3 -> 1, 17 -> 0 (clamped to [0, 5])."""
     import paper_2010_10039_gb300 as huff
     assert huff.huff_reduce_factor(1.02717, 32) == 4
     assert huff.huff_reduce_factor(2.73, 32) == 3
@@ -53,7 +53,10 @@ def test_reduce_factor_rule(lib):
     assert huff.huff_reduce_factor(4.14, 32) == 2
     assert huff.huff_reduce_factor(5.2, 32) == 2
     assert huff.huff_reduce_factor(8.3, 32) == 1
+    assert huff.huff_reduce_factor(17.0, 32) == 0
+    assert huff.huff_reduce_factor(40.0, 32) == 0
     assert huff.huff_reduce_factor(0.3, 32) == 5
+    assert huff.huff_reduce_factor(1.5, 16) == 3
 
 
 def test_workspace_grows_with_n(lib):
