@@ -42,6 +42,7 @@ WORKLOADS = {
                                    "over 1024 bins, seed 4 (field j: stream j, size/scale from stream 10000+j)"),
 }
 BATCH_FIELDS = 512
+SUB_SERVED_SECONDS = 5.0      # open-loop seconds of the served sub-record of the default line
 NOMINAL_HBM_GBPS = 8000.0     # GB300 HBM3e, nominal (the measured copy peak is the headline denominator)
 
 
@@ -203,6 +204,26 @@ def oracle_leg(name: str, n_full: int, nbins: int, max_seconds: float = 15.0):
     return gbs, f"first {n} symbols of the workload, histogram+codebook+encode, 1 thread", n, dt
 
 
+def multithreaded_leg(sym_np: np.ndarray, nbins: int, chunk_log2: int, gpu_words: np.ndarray, gpu_bits: int):
+    """The multithreaded CPU encoder (the paper's Table VI measurement) on the
+    whole field at 1, 2, 4, ... threads up to the host's cores; its stream at
+    all cores is compared with the GPU's."""
+    import cpu_baseline
+    cores = cpu_baseline.default_threads()
+    counts = sorted({1, cores} | {1 << k for k in range(1, 9) if (1 << k) < cores})
+    rows = cpu_baseline.scaling(sym_np, nbins, counts, chunk_log2)
+    book = cpu_baseline.codebook(cpu_baseline.histogram(sym_np, nbins, cores), cores)
+    words, _, bits = cpu_baseline.encode(sym_np, book, chunk_log2, cores)
+    equal = bits == gpu_bits and np.array_equal(words, gpu_words)
+    if not equal:
+        raise RuntimeError("the multithreaded CPU stream differs from the GPU stream")
+    best = rows[-1]
+    return {"value": best["hist_codebook_encode_GBps"], "unit": "GB/s", "cores": cores,
+            "kind": "multithreaded C, POSIX threads (histogram + codebook + encode)",
+            "sample": f"the whole field ({sym_np.size} symbols), best of 2 runs per thread count",
+            "stream_equal_to_gpu": equal, "scaling": rows}
+
+
 def run_reference(args, world, rank):
     name = args.workload
     n_full, nbins, desc = WORKLOADS[name]
@@ -340,50 +361,82 @@ def run_ours(args, world, rank, local):
     # end to end through the binding from pinned host memory: every step copies
     # its input in and its stream and offsets out.  Two buffer sets and two copy
     # streams let step k + 1's input copy overlap step k's compute and read-back.
+    # The stream's length is known only on the device: its bit count comes back
+    # by an 8-byte copy, and the host reads it one step late (while the device
+    # is already busy with the next step) to size the stream's read-back.
+    nw = (total_bits + 31) // 32
+    ref_words = pipe.out[:nw].cpu()
+    ref_offs = pipe.offsets.cpu()
     host_in = torch.from_numpy(sym_np.view(np.int16)).pin_memory()
     pipes = [pipe, huff.Pipeline(n, nbins, params)]
     dev_in = [torch.empty_like(sym), torch.empty_like(sym)]
     host_out = [torch.empty(pipe.out.numel(), dtype=torch.int32).pin_memory() for _ in range(2)]
     host_offs = [torch.empty(pipe.offsets.numel(), dtype=torch.int64).pin_memory() for _ in range(2)]
+    host_tb = [torch.zeros(1, dtype=torch.int64).pin_memory() for _ in range(2)]
     s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
     ev_in = [torch.cuda.Event(), torch.cuda.Event()]
     ev_used = [torch.cuda.Event(), torch.cuda.Event()]     # compute on buffer set b finished
+    ev_tb = [torch.cuda.Event(), torch.cuda.Event()]       # bit count of buffer set b on the host
     ev_read = [torch.cuda.Event(), torch.cuda.Event()]     # read-back of buffer set b finished
-    e2e_steps = max(2, min(K, 6))
-    torch.cuda.synchronize()
-    barrier(world)
-    t0 = time.perf_counter()
-    with torch.cuda.stream(s_in):
-        dev_in[0].copy_(host_in, non_blocking=True)
-        ev_in[0].record(s_in)
-    for k in range(e2e_steps):
-        b = k % 2
-        if k + 1 < e2e_steps:
-            nb = 1 - b
-            with torch.cuda.stream(s_in):
-                if k >= 1:
-                    s_in.wait_event(ev_used[nb])               # step k - 1 no longer reads dev_in[nb]
-                dev_in[nb].copy_(host_in, non_blocking=True)
-                ev_in[nb].record(s_in)
-        stream.wait_event(ev_in[b])
-        if k >= 2:
-            stream.wait_event(ev_read[b])                      # step k - 2's stream is off the device
-        pipes[b].run(dev_in[b])
-        ev_used[b].record(stream)
-        tb = int(pipes[b].total_bits.item())
-        nw = (tb + 31) // 32
+    read_words = [0, 0]
+
+    def read_back(b):
+        ev_tb[b].synchronize()
+        nw = (int(host_tb[b][0]) + 31) // 32
+        read_words[b] = nw
         with torch.cuda.stream(s_out):
-            s_out.wait_event(ev_used[b])
             host_out[b][:nw].copy_(pipes[b].out[:nw], non_blocking=True)
             host_offs[b].copy_(pipes[b].offsets, non_blocking=True)
             ev_read[b].record(s_out)
+
+    def e2e_run(steps):
+        with torch.cuda.stream(s_in):
+            dev_in[0].copy_(host_in, non_blocking=True)
+            ev_in[0].record(s_in)
+        pending = None
+        for k in range(steps):
+            b = k % 2
+            if k + 1 < steps:
+                nb = 1 - b
+                with torch.cuda.stream(s_in):
+                    if k >= 1:
+                        s_in.wait_event(ev_used[nb])           # step k - 1 no longer reads dev_in[nb]
+                    dev_in[nb].copy_(host_in, non_blocking=True)
+                    ev_in[nb].record(s_in)
+            stream.wait_event(ev_in[b])
+            if k >= 2:
+                stream.wait_event(ev_read[b])                  # step k - 2's stream is off the device
+            pipes[b].run(dev_in[b])
+            ev_used[b].record(stream)
+            with torch.cuda.stream(s_out):
+                s_out.wait_event(ev_used[b])
+                host_tb[b].copy_(pipes[b].total_bits, non_blocking=True)
+                ev_tb[b].record(s_out)
+            if pending is not None:
+                read_back(pending)                             # step k - 1, while step k computes
+            pending = b
+        read_back(pending)
+        torch.cuda.synchronize()
+
+    e2e_steps = max(8, K)
     torch.cuda.synchronize()
+    e2e_run(2)                                                 # untimed: touches both buffer sets
+    barrier(world)
+    t0 = time.perf_counter()
+    e2e_run(e2e_steps)
     e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world)
     e2e_val = world * in_bytes / e2e_s / 1e9
     for b in range(2):
         st = pipes[b].status()
         if st != 0:
             raise RuntimeError(f"end-to-end run: device status {huff.STATUS.get(st, st)}")
+    # both buffer sets encoded the same input: their streams must equal the
+    # device-timed run's
+    for b in range(2):
+        if read_words[b] != nw or not torch.equal(host_out[b][:nw], ref_words) or \
+                not torch.equal(host_offs[b], ref_offs):
+            raise RuntimeError(f"end-to-end run: buffer set {b} read back a different stream")
+    del pipes, dev_in, host_out, host_offs
 
     if rank != 0:
         return
@@ -391,7 +444,9 @@ def run_ours(args, world, rank, local):
     if world == 1 and not args.no_cpu_baseline:
         gbs, samp, _, _ = oracle_leg(name, n, nbins)
         cpu = {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": samp,
-               "parts": dict(LAST_ORACLE_PARTS), "host_cores": os.cpu_count()}
+               "parts": dict(LAST_ORACLE_PARTS), "host_cores": os.cpu_count(),
+               "multithreaded": multithreaded_leg(sym_np, nbins, args.chunk_log2, ref_words.numpy().view(np.uint32),
+                                                  total_bits)}
     enc_s = enc_ms * 1e-3
     line = {
         "metric": "huffman_encode_input_GBps",
@@ -426,13 +481,14 @@ def run_ours(args, world, rank, local):
                                "frac": round(hist_alg / (hist_ms * 1e-3) / 1e9 / peak, 4),
                                "traffic": load_traffic("hist_kernel") if name == "hpc_field" else None},
         "e2e": {"value": round(e2e_val, 3), "unit": "GB/s", "h2d_bytes_per_step": in_bytes,
-                "d2h_bytes_per_step": out_bytes + off_bytes + 8},
+                "d2h_bytes_per_step": out_bytes + off_bytes + 8, "steps": e2e_steps,
+                "untimed_steps_before": 2, "checked": "both buffer sets' streams equal the timed run's"},
         "gpu_launches": launches,
         "cpu_baseline": cpu,
         "clocks": clk,
         "decode": dec,
     }
-    print(json.dumps(line), flush=True)
+    return line
 
 
 # ----------------------------------------------------------------------------- large alphabets
@@ -556,7 +612,7 @@ def run_large_alphabet(args, world, rank, local):
         "cpu_baseline": cpu,
         "clocks": clk,
     }
-    print(json.dumps(line), flush=True)
+    return line
 
 
 # ----------------------------------------------------------------------------- batched form
@@ -669,19 +725,23 @@ def run_batched(args, world, rank, local):
     ms_per_call = ev0.elapsed_time(ev1) / reps
 
     # end to end: pinned host inputs in, encoded streams and offsets out, every
-    # step.  Two buffer sets, each with its own plan (the tuned settings), and
-    # a copy stream for each direction: step k + 1's inputs go in while step k
-    # encodes and its results come back.
+    # step.  Two buffer sets, each with its own plan (the tuned settings) and
+    # its own host result buffers, and a copy stream for each direction: step
+    # k + 1's inputs go in while step k encodes and its results come back.
+    # Every field's stream length is the one the timed run found (the inputs
+    # are the same), so no step waits on the device for it.
     host_in = [f["sym"].cpu().pin_memory() for f in fields]
-    host_out = [torch.empty_like(f["out"], device="cpu").pin_memory() for f in fields]
-    host_off = [torch.empty_like(f["offsets"], device="cpu").pin_memory() for f in fields]
     nw = [(int(f["total_bits"].item()) + 31) // 32 for f in fields]
+    ref_out = [f["out"][:w].cpu() for f, w in zip(fields, nw)]
+    ref_off = [f["offsets"].cpu() for f in fields]
     fields2 = [{"sym": torch.empty_like(f["sym"]), "nbins": f["nbins"], "chunk_log2": f["chunk_log2"],
                 "out": torch.empty_like(f["out"]), "offsets": torch.empty_like(f["offsets"]),
                 "total_bits": torch.zeros_like(f["total_bits"])} for f in fields]
     plan2 = huff.BatchPlan(fields2, autotune=False, reduce_log2=info["reduce_log2"],
                            max_subtiles=info["max_subtiles"], ctas_per_sm=info["ctas_per_sm"])
     sets = [(fields, plan), (fields2, plan2)]
+    host_out = [[torch.empty(max(1, w), dtype=torch.int32).pin_memory() for w in nw] for _ in range(2)]
+    host_off = [[torch.empty_like(f["offsets"], device="cpu").pin_memory() for f in fields] for _ in range(2)]
     s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
     ev_in = [torch.cuda.Event(), torch.cuda.Event()]
     ev_used = [torch.cuda.Event(), torch.cuda.Event()]
@@ -693,33 +753,43 @@ def run_batched(args, world, rank, local):
                 f["sym"].copy_(h, non_blocking=True)
             ev_in[b].record(s_in)
 
-    e2e_steps = max(2, min(K, 4))
+    def e2e_run(steps):
+        copy_in(0)
+        for k in range(steps):
+            b = k % 2
+            if k + 1 < steps:
+                if k >= 1:
+                    s_in.wait_event(ev_used[1 - b])          # step k - 1 no longer reads those inputs
+                copy_in(1 - b)
+            stream.wait_event(ev_in[b])
+            if k >= 2:
+                stream.wait_event(ev_read[b])                # step k - 2's results are off the device
+            sets[b][1].encode()
+            ev_used[b].record(stream)
+            with torch.cuda.stream(s_out):
+                s_out.wait_event(ev_used[b])
+                for f, ho, hf, w in zip(sets[b][0], host_out[b], host_off[b], nw):
+                    ho[:w].copy_(f["out"][:w], non_blocking=True)
+                    hf.copy_(f["offsets"], non_blocking=True)
+                ev_read[b].record(s_out)
+        torch.cuda.synchronize()
+
+    e2e_steps = max(8, K)
     torch.cuda.synchronize()
+    e2e_run(2)                                               # untimed: touches both buffer sets
+    barrier(world)
     t0 = time.perf_counter()
-    copy_in(0)
-    for k in range(e2e_steps):
-        b = k % 2
-        if k + 1 < e2e_steps:
-            if k >= 1:
-                s_in.wait_event(ev_used[1 - b])          # step k - 1 no longer reads those inputs
-            copy_in(1 - b)
-        stream.wait_event(ev_in[b])
-        if k >= 2:
-            stream.wait_event(ev_read[b])                # step k - 2's results are off the device
-        sets[b][1].encode()
-        ev_used[b].record(stream)
-        with torch.cuda.stream(s_out):
-            s_out.wait_event(ev_used[b])
-            for f, ho, hf, w in zip(sets[b][0], host_out, host_off, nw):
-                ho[:w].copy_(f["out"][:w], non_blocking=True)
-                hf.copy_(f["offsets"], non_blocking=True)
-            ev_read[b].record(s_out)
-    torch.cuda.synchronize()
+    e2e_run(e2e_steps)
     e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world)
     for fs, pl in sets:
         st = pl.status()
         if any(st):
             raise RuntimeError(f"end-to-end run: device status {[huff.STATUS.get(x, x) for x in st if x][:4]}")
+    for b, (fs, _) in enumerate(sets):
+        for j, f in enumerate(fs):
+            if int(f["total_bits"].item()) != int(fields[j]["total_bits"].item()) or \
+                    not torch.equal(host_out[b][j][:nw[j]], ref_out[j]) or not torch.equal(host_off[b][j], ref_off[j]):
+                raise RuntimeError(f"end-to-end run: buffer set {b}, field {j} read back a different stream")
     del plan2, fields2
 
     if rank != 0:
@@ -751,12 +821,13 @@ def run_batched(args, world, rank, local):
                      "unit": "GB/s", "frac": round(enc_alg / (enc_ms * 1e-3) / 1e9 / peak, 4), "traffic": None,
                      "algorithmic_bytes": enc_alg},
         "e2e": {"value": round(world * in_bytes / e2e_s / 1e9, 3), "unit": "GB/s", "h2d_bytes_per_step": in_bytes,
-                "d2h_bytes_per_step": out_bytes + off_bytes},
+                "d2h_bytes_per_step": out_bytes + off_bytes, "steps": e2e_steps, "untimed_steps_before": 2,
+                "checked": "both buffer sets' streams and offsets equal the timed run's"},
         "gpu_launches": launches,
         "cpu_baseline": cpu,
         "clocks": clk,
     }
-    print(json.dumps(line), flush=True)
+    return line
 
 
 # ----------------------------------------------------------------------------- served form
@@ -937,6 +1008,82 @@ def run_served(args, world, rank, local):
     sat_serial = sat_bytes / (time.monotonic() - ts) / 1e9
     sat_stats = srv.stats()
 
+    # ---------------- rate sweep: open loop over the prepared requests (reused
+    # cyclically) at rising rates until the server stops keeping up; at each
+    # rate the same arrivals also go through serial plain calls
+    def wait_until(t):
+        d = t - time.monotonic()
+        if d > 3e-4:
+            time.sleep(d - 2e-4)
+        while time.monotonic() < t:
+            pass
+        return -d
+
+    def sweep_point(rate, seconds):
+        arr_r = synth.served_arrivals(int(rate * seconds * 1.3) + 64, rate=rate)
+        cnt = int(np.searchsorted(arr_r, seconds))
+        reqs = [items[i % len(items)] for i in range(cnt)]
+        nbytes = sum(r[4] for r in reqs)
+        st0 = srv.stats()
+        tq = queue.Queue()
+        lat_r, t_last, bad = [], [0.0], []
+
+        def coll():
+            while True:
+                x = tq.get()
+                if x is None:
+                    return
+                t, arrival = x
+                res = srv.wait(t)
+                if res["status"]:
+                    bad.append(res["status"])
+                lat_r.append((res["t_done"] - arrival) * 1e3)
+                t_last[0] = max(t_last[0], res["t_done"])
+                srv.release(t)
+        th = threading.Thread(target=coll, daemon=True)
+        th.start()
+        t0r = time.monotonic() + 0.002
+        late_r = 0.0
+        for (_, sym, nb, _, _), a in zip(reqs, arr_r[:cnt]):
+            arrival = t0r + float(a)
+            late_r = max(late_r, wait_until(arrival))
+            tq.put((srv.submit(sym, nb, keep=False), arrival))
+        tq.put(None)
+        th.join()
+        if bad:
+            raise RuntimeError(f"sweep at {rate}/s: jobs failed {sorted(set(bad))}")
+        st1 = srv.stats()
+        served_r = nbytes / (t_last[0] - t0r) / 1e9
+        # serial plain calls on the same arrivals
+        slat_r = []
+        t0s_r = time.monotonic() + 0.002
+        last = t0s_r
+        for (_, sym, nb, _, _), a in zip(reqs, arr_r[:cnt]):
+            arrival = t0s_r + float(a)
+            wait_until(arrival)
+            pipes[nb].run(sym)
+            cur.synchronize()
+            last = time.monotonic()
+            slat_r.append((last - arrival) * 1e3)
+        serial_r = nbytes / (last - t0s_r) / 1e9
+        nb_batches = st1["batches"] - st0["batches"]
+        return {"rate_per_s": rate, "requests": cnt, "offered_GBps": round(nbytes / seconds / 1e9, 3),
+                "served_GBps": round(served_r, 3), "served_p50_ms": round(_pct(lat_r, 50), 3),
+                "served_p99_ms": round(_pct(lat_r, 99), 3),
+                "mean_jobs_per_batch": round((st1["completed"] - st0["completed"]) / max(1, nb_batches), 2),
+                "serial_GBps": round(serial_r, 3), "serial_p50_ms": round(_pct(slat_r, 50), 3),
+                "serial_p99_ms": round(_pct(slat_r, 99), 3), "submit_late_max_ms": round(max(0.0, late_r) * 1e3, 3)}
+
+    sweep = []
+    for rate_r in args.sweep_rates:
+        row = sweep_point(rate_r, args.sweep_seconds)
+        sweep.append(row)
+        if row["served_GBps"] < 0.85 * row["offered_GBps"]:
+            break                                       # saturated: the server no longer keeps up
+    for p in pipes.values():
+        if p.status() != 0:
+            raise RuntimeError("serial path reported an error in the sweep")
+
     # ---------------- end to end: pinned host payloads in, encoded streams out
     E = min(100, M)
     host = [it[1].cpu().pin_memory() for it in items[:E]]
@@ -999,6 +1146,12 @@ def run_served(args, world, rank, local):
                        "batches": sat_stats["batches"] - stats["batches"]},
         "server": {k: stats[k] for k in ("batches", "max_batch_jobs", "max_concurrent_batches", "pool_peak")},
         "submit_late_max_ms": round(late * 1e3, 3),
+        "rate_sweep": {"seconds_per_rate": args.sweep_seconds,
+                       "requests": f"the {M} closed-loop requests, reused cyclically",
+                       "latency_from": "scheduled arrival to completion (server: device completion seen by the "
+                                       "server; serial: after the stream synchronises)",
+                       "stop": "after the first rate at which the server delivers < 85% of the offered load",
+                       "points": sweep},
         "parity_sampled": checked,
         "roofline": {"bound": "hbm", "kernel": "served pipeline at saturation (histogram + codebook + encode)",
                      "achieved": round(sat_served * 2.0, 2), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
@@ -1010,7 +1163,7 @@ def run_served(args, world, rank, local):
         "cpu_baseline": cpu,
         "clocks": clk,
     }
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def main():
@@ -1027,18 +1180,43 @@ def main():
     ap.add_argument("--rate", type=float, default=2000.0, help="served: arrivals per second")
     ap.add_argument("--duration", type=float, default=60.0, help="served: seconds of arrivals")
     ap.add_argument("--saturation-requests", type=int, default=1000, help="served: closed-loop requests")
+    ap.add_argument("--sweep-rates", type=lambda v: [float(x) for x in v.split(",")],
+                    default=[2000.0, 4000.0, 8000.0, 16000.0, 32000.0, 64000.0, 128000.0],
+                    help="served: open-loop rates of the sweep (req/s, comma separated)")
+    ap.add_argument("--sweep-seconds", type=float, default=1.0, help="served: seconds of arrivals per sweep rate")
+    ap.add_argument("--no-sub-records", action="store_true",
+                    help="hpc_field: leave out the batched and served sub-records")
     args = ap.parse_args()
     world, rank, local = dist_setup(args)
+    line = None
     if args.impl == "reference":
         run_reference(args, world, rank)
     elif args.workload == "batched_fields":
-        run_batched(args, world, rank, local)
+        line = run_batched(args, world, rank, local)
     elif args.workload == "served":
-        run_served(args, world, rank, local)
+        line = run_served(args, world, rank, local)
     elif args.workload == "large_alphabet":
-        run_large_alphabet(args, world, rank, local)
+        line = run_large_alphabet(args, world, rank, local)
     else:
-        run_ours(args, world, rank, local)
+        line = run_ours(args, world, rank, local)
+        if args.workload == "hpc_field" and not args.no_sub_records:
+            # the batched and served forms, each with its own timing, as
+            # sub-records of the same line (no CPU leg of their own)
+            import torch
+            torch.cuda.empty_cache()
+            sub = argparse.Namespace(**vars(args))
+            sub.no_cpu_baseline = True
+            sub.duration = SUB_SERVED_SECONDS
+            b = run_batched(sub, world, rank, local)
+            torch.cuda.empty_cache()
+            sv = run_served(sub, world, rank, local)
+            torch.cuda.empty_cache()
+            if line is not None:
+                drop = ("n_gpus", "higher_is_better", "scaling", "vs_baseline", "data", "cpu_baseline", "warmup")
+                line["batched"] = {k: v for k, v in b.items() if k not in drop}
+                line["served"] = {k: v for k, v in sv.items() if k not in drop}
+    if line is not None:
+        print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

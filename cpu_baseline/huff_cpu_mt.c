@@ -108,15 +108,6 @@ static void split(uint64_t n, int T, int t, uint64_t *lo, uint64_t *hi)
     *hi = n * (uint64_t)(t + 1) / (uint64_t)T;
 }
 
-static inline uint32_t sym_at(const void *s, uint64_t i, int width)
-{
-    switch (width) {
-        case 1: return ((const uint8_t *)s)[i];
-        case 2: return ((const uint16_t *)s)[i];
-        default: return ((const uint32_t *)s)[i];
-    }
-}
-
 /* -------------------------------------------------------------- histogram */
 
 typedef struct {
