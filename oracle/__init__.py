@@ -56,9 +56,10 @@ def _bind(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.oracle_lengths_heap.argtypes = [vp, u32, vp]
     lib.oracle_canonical.argtypes = [vp, u32, vp, vp, vp, vp, vp, vp]
     lib.oracle_encode.argtypes = [vp, u64, i32, vp, vp, u32, i32, vp, u64, vp, vp]
+    lib.oracle_encode_format.argtypes = [vp, u64, i32, vp, vp, u32, i32, i32, i32, vp, u64, vp, vp]
     lib.oracle_decode.argtypes = [vp, u64, u64, vp, vp, vp, vp, u32, i32, vp]
     for f in (lib.oracle_histogram, lib.oracle_lengths_two_queue, lib.oracle_lengths_heap,
-              lib.oracle_canonical, lib.oracle_encode, lib.oracle_decode):
+              lib.oracle_canonical, lib.oracle_encode, lib.oracle_encode_format, lib.oracle_decode):
         f.restype = i32
     return lib
 
@@ -141,6 +142,30 @@ def encode(sym: np.ndarray, book: dict, chunk_log2: int = 10, capacity_words: in
                                  _ptr(offs), _ptr(total)))
     tb = int(total[0])
     return out[:(tb + 31) // 32].copy(), offs, tb
+
+
+UNIT_DTYPE = {8: np.uint8, 16: np.uint16, 32: np.uint32}
+
+
+def encode_format(sym: np.ndarray, book: dict, chunk_log2: int = 10, word_bits: int = 32, aligned: bool = False):
+    """The stream as W-bit typed units (Sec. IV-C typed cells), dense or with
+    each chunk starting at a unit boundary (Sec. VI un-gathered chunks).
+    Returns (units uintW[used], offsets uint64[nchunks+1], total_bits): dense
+    offsets are bits, chunk-aligned offsets are units; total_bits counts the
+    padding of the chunk-aligned form."""
+    sym = np.ascontiguousarray(sym)
+    n = sym.size
+    W = int(word_bits)
+    nchunks = (n + (1 << chunk_log2) - 1) >> chunk_log2
+    cap_units = (n * max(1, book["max_len"]) + W - 1) // W + (nchunks if aligned else 0)
+    out = np.zeros(max(1, cap_units), dtype=UNIT_DTYPE.get(W, np.uint32))
+    offs = np.zeros(nchunks + 1, dtype=np.uint64)
+    total = np.zeros(1, dtype=np.uint64)
+    _check(_load().oracle_encode_format(_ptr(sym), n, _width(sym), _ptr(book["code"]), _ptr(book["len"]),
+                                        book["nbins"], chunk_log2, W, 1 if aligned else 0, _ptr(out), cap_units,
+                                        _ptr(offs), _ptr(total)))
+    tb = int(total[0])
+    return out[:(tb + W - 1) // W].copy(), offs, tb
 
 
 def decode(stream: np.ndarray, total_bits: int, n: int, book: dict, width: int = 2) -> np.ndarray:

@@ -19,6 +19,11 @@
  *                                           operator's order: a_{2k+1} right
  *                                           after a_{2k}) into one dense
  *                                           MSB-first bitstream, chunk offsets
+ *   oracle_encode_format      Sec. IV-C,    the same concatenation written as
+ *                             Sec. VI       typed units of W = 8, 16 or 32
+ *                                           bits, dense or with every chunk
+ *                                           starting at a unit boundary (the
+ *                                           un-gathered chunks)
  *   oracle_decode             Sec. IV-B2    treeless canonical decoding with
  *                                           First and Entry
  *
@@ -31,7 +36,11 @@
  *  - canonical orientation as Sec. IV-B2 asks (a short codeword is numerically
  *    larger than the same-length prefix of any longer one), codewords of one
  *    length in ascending symbol id;
- *  - the bitstream is an array of 32-bit words, bit 31 of word 0 first.
+ *  - the bitstream is an array of 32-bit words, bit 31 of word 0 first;
+ *  - a stream of W-bit typed units holds the same bits, bit W-1 of unit 0
+ *    first; in the chunk-aligned form a chunk's last unit is padded with zero
+ *    bits and its offset counts units, and the stream's length counts the
+ *    padding.
  *
  * Error returns (negative): -1 bad argument, -2 symbol >= nbins, -3 symbol
  * without codeword, -4 output capacity too small, -5 histogram sum >= 2^32,
@@ -312,6 +321,65 @@ int oracle_encode(const void *sym, uint64_t n, int width, const uint64_t *code, 
         }
     }
     chunk_bit_offset[c] = p;
+    *total_bits = p;
+    return 0;
+}
+
+/* ----------------------------------------------------------- typed units */
+
+/*
+ * Codewords in input order, most significant bit first, into an array of
+ * W-bit units (the typed data cells of Sec. IV-C, W in {8, 16, 32}); bit W-1
+ * of unit 0 is stream bit 0.  aligned = 0: one dense stream, offs[c] = stream
+ * bit of symbol c * 2^chunk_log2, total = bits.  aligned = 1: the gathered
+ * chunks keep their own units (Sec. VI: the chunks before the optional dense
+ * gathering): chunk c starts at unit offs[c], its last unit is zero-padded,
+ * the final entry and total / W are the stream's units.  out holds cap_units
+ * units of W bits (a uint8, uint16 or uint32 array).
+ */
+static void put_unit_bit(void *out, int W, uint64_t p, uint32_t bit)
+{
+    uint64_t u = p / (uint64_t)W;
+    uint32_t k = (uint32_t)(W - 1 - (int)(p % (uint64_t)W));
+    if (W == 8) ((uint8_t *)out)[u] |= (uint8_t)(bit << k);
+    else if (W == 16) ((uint16_t *)out)[u] |= (uint16_t)(bit << k);
+    else ((uint32_t *)out)[u] |= bit << k;
+}
+
+static void zero_unit(void *out, int W, uint64_t u)
+{
+    if (W == 8) ((uint8_t *)out)[u] = 0;
+    else if (W == 16) ((uint16_t *)out)[u] = 0;
+    else ((uint32_t *)out)[u] = 0;
+}
+
+int oracle_encode_format(const void *sym, uint64_t n, int width, const uint64_t *code, const uint8_t *len,
+                         uint32_t nbins, int chunk_log2, int word_bits, int aligned, void *out,
+                         uint64_t cap_units, uint64_t *offs, uint64_t *total_bits)
+{
+    const int W = word_bits;
+    if (chunk_log2 < 0 || chunk_log2 > 40 || (W != 8 && W != 16 && W != 32) || (aligned != 0 && aligned != 1))
+        return -1;
+    uint64_t chunk = 1ull << chunk_log2;
+    uint64_t p = 0, c = 0;
+    for (uint64_t i = 0; i < n; i++) {
+        if (i % chunk == 0) {
+            if (aligned) p = (p + (uint64_t)W - 1) / (uint64_t)W * (uint64_t)W;   /* next unit boundary */
+            offs[c++] = aligned ? p / (uint64_t)W : p;
+        }
+        uint32_t s = load_sym(sym, i, width);
+        if (s >= nbins) return -2;
+        uint32_t l = len[s];
+        if (l == 0) return -3;
+        for (int b = (int)l - 1; b >= 0; b--) {
+            if (p / (uint64_t)W >= cap_units) return -4;
+            if (p % (uint64_t)W == 0) zero_unit(out, W, p / (uint64_t)W);
+            put_unit_bit(out, W, p, (uint32_t)((code[s] >> b) & 1u));
+            p++;
+        }
+    }
+    if (aligned) p = (p + (uint64_t)W - 1) / (uint64_t)W * (uint64_t)W;
+    offs[c] = aligned ? p / (uint64_t)W : p;
     *total_bits = p;
     return 0;
 }

@@ -31,7 +31,10 @@ MUTANTS = [
      "first[l] = (first[l + 1] + count[l + 1]) >> 1;"),
     ("entry_wrong_index", "entry[l + 1] = entry[l] + count[l];", "entry[l + 1] = entry[l] + count[l + 1];"),
     ("codes_in_descending_id", "code[k] = first[l] + next[l];", "code[k] = first[l] + count[l] - 1 - next[l];"),
-    ("codeword_lsb_first", "for (int b = (int)l - 1; b >= 0; b--) {", "for (int b = 0; b < (int)l; b++) {"),
+    ("codeword_lsb_first", "for (int b = (int)l - 1; b >= 0; b--) {\n            uint64_t w = p >> 5;",
+     "for (int b = 0; b < (int)l; b++) {\n            uint64_t w = p >> 5;"),
+    ("unit_codeword_lsb_first", "for (int b = (int)l - 1; b >= 0; b--) {\n            if (p / (uint64_t)W",
+     "for (int b = 0; b < (int)l; b++) {\n            if (p / (uint64_t)W"),
     ("word_lsb_first", "out[w] |= bit << (31 - (p & 31));", "out[w] |= bit << (p & 31);"),
     ("chunk_offset_after_symbol", "if (i % chunk == 0) chunk_bit_offset[c++] = p;",
      "if (i % chunk == 0) chunk_bit_offset[c++] = p + len[load_sym(sym, i, width) % nbins];"),
@@ -39,6 +42,13 @@ MUTANTS = [
      "uint32_t s = sorted_syms[entry[l] + (v - first[l]) + (l > 1)];"),
     ("single_symbol_length_two", "if (m == 1) { len[leaf[0].id] = 1; free(leaf); return 1; }",
      "if (m == 1) { len[leaf[0].id] = 2; free(leaf); return 2; }"),
+    ("unit_lsb_first", "uint32_t k = (uint32_t)(W - 1 - (int)(p % (uint64_t)W));",
+     "uint32_t k = (uint32_t)(p % (uint64_t)W);"),
+    ("aligned_offsets_in_bits", "offs[c++] = aligned ? p / (uint64_t)W : p;", "offs[c++] = p;"),
+    ("aligned_stream_not_padded_at_end", "    if (aligned) p = (p + (uint64_t)W - 1) / (uint64_t)W * (uint64_t)W;\n    offs[c]",
+     "    offs[c]"),
+    ("dense_form_padded_too", "if (aligned) p = (p + (uint64_t)W - 1) / (uint64_t)W * (uint64_t)W;   /* next unit boundary */",
+     "p = (p + (uint64_t)W - 1) / (uint64_t)W * (uint64_t)W;"),
 ]
 
 RUNNER = textwrap.dedent('''
@@ -59,6 +69,8 @@ RUNNER = textwrap.dedent('''
         ("concatenation", lambda: [P.test_encode_matches_string_concatenation(n, c)
                                    for n, c in ((1025, 3), (5000, 10))]),
         ("round_trip", lambda: P.test_round_trip_synthetic_fields()),
+        ("units", lambda: [P.test_encode_format_matches_string_definition(W, a, n, c)
+                           for W in (8, 16) for a in (False, True) for n, c in ((37, 3), (1025, 6))]),
     ]
     failed = []
     for name, fn in checks:

@@ -343,3 +343,88 @@ def test_round_trip_synthetic_fields():
         words, offs, tb = oracle.encode(sym, book, chunk_log2=10)
         assert tb == int((h.astype(np.int64) * book["len"]).sum())
         assert np.array_equal(oracle.decode(words, tb, sym.size, book, width=sym.itemsize), sym)
+
+
+# ------------------------------------------------------------------ typed units
+
+def _naive_units(sym, book, chunk_log2, W, aligned):
+    """The definition written out with Python strings: chunk bit strings, each
+    padded to a unit boundary in the aligned form, cut into W-bit units."""
+    n = sym.size
+    out, offs = "", []
+    for c0 in range(0, n, 1 << chunk_log2):
+        if aligned:
+            out += "0" * ((-len(out)) % W)
+        offs.append(len(out) // W if aligned else len(out))
+        out += _naive_bits(sym[c0:c0 + (1 << chunk_log2)], book)
+    if aligned:
+        out += "0" * ((-len(out)) % W)
+    offs.append(len(out) // W if aligned else len(out))
+    total = len(out)
+    padded = out + "0" * ((-len(out)) % W)
+    units = [int(padded[i:i + W], 2) for i in range(0, len(padded), W)]
+    return units, offs, total
+
+
+@pytest.mark.parametrize("W", [8, 16, 32])
+@pytest.mark.parametrize("aligned", [False, True])
+@pytest.mark.parametrize("n,chunk_log2", [(0, 3), (1, 3), (37, 3), (1000, 4), (1025, 6), (3001, 10)])
+def test_encode_format_matches_string_definition(W, aligned, n, chunk_log2):
+    rng = np.random.default_rng(7 * n + W + chunk_log2 + (100 if aligned else 0))
+    sym = rng.choice(40, size=n, p=np.arange(40, 0, -1) / np.arange(40, 0, -1).sum()).astype(np.uint16)
+    h = np.bincount(sym, minlength=40).astype(np.uint32)
+    if n == 0:
+        h[:] = 1
+    book = oracle.codebook(h)
+    units, offs, tb = oracle.encode_format(sym, book, chunk_log2, W, aligned)
+    want_units, want_offs, want_tb = _naive_units(sym, book, chunk_log2, W, aligned)
+    assert units.dtype == oracle.UNIT_DTYPE[W]
+    assert [int(u) for u in units] == want_units
+    assert offs.tolist() == want_offs
+    assert tb == want_tb
+
+
+def test_encode_format_dense_units_are_the_big_endian_words():
+    """Dense 8- and 16-bit units are the 32-bit stream's words split most
+    significant part first; 32-bit units are the words themselves."""
+    from paper_2010_10039_gb300 import synth
+    sym = synth.laplace_field(20_011, seed=9)
+    book = oracle.codebook(oracle.histogram(sym, 1024))
+    words, offs, tb = oracle.encode(sym, book, chunk_log2=10)
+    be = words.astype(">u4").tobytes()
+    for W in (8, 16, 32):
+        units, o, t = oracle.encode_format(sym, book, 10, W, False)
+        assert t == tb and np.array_equal(o, offs)
+        want = np.frombuffer(be, dtype=f">u{W // 8}")[: (tb + W - 1) // W]
+        assert np.array_equal(units, want.astype(oracle.UNIT_DTYPE[W]))
+
+
+@pytest.mark.parametrize("W", [8, 16, 32])
+def test_encode_format_aligned_chunks_decode_alone(W):
+    """Every chunk of the aligned form starts at its offset and decodes on its
+    own to its symbols; the padding between chunks is zero and shorter than a
+    unit."""
+    from paper_2010_10039_gb300 import synth
+    sym = synth.gaussian_field(9_000, seed=4)
+    book = oracle.codebook(oracle.histogram(sym, 1024))
+    M = 9
+    units, offs, tb = oracle.encode_format(sym, book, M, W, True)
+    assert tb == int(offs[-1]) * W and units.size == int(offs[-1])
+    bits = "".join(format(int(u), f"0{W}b") for u in units)
+    for c in range(offs.size - 1):
+        chunk = sym[c << M:(c + 1) << M]
+        body = _naive_bits(chunk, book)
+        seg = bits[int(offs[c]) * W:int(offs[c + 1]) * W]
+        assert seg.startswith(body) and set(seg[len(body):]) <= {"0"} and len(seg) - len(body) < W
+        words = _pack(body)
+        assert oracle.decode(np.array(words, np.uint32), len(body), chunk.size, book, width=2).tolist() == \
+            chunk.tolist()
+
+
+def test_encode_format_errors():
+    book = oracle.codebook(np.array([3, 0, 2], dtype=np.uint32))
+    sym = np.array([0, 2, 0, 2], dtype=np.uint16)
+    with pytest.raises(oracle.OracleError):
+        oracle.encode_format(sym, book, 3, 12, False)               # not a unit width
+    with pytest.raises(oracle.OracleError):
+        oracle.encode_format(np.array([1], np.uint16), book, 3, 8, True)   # no codeword
