@@ -358,6 +358,37 @@ def run_ours(args, world, rank, local):
                "equal_to_input": True}
         del dec_out
 
+    # format ablation: the encode alone in each stream format (Sec. IV-C typed
+    # units of W bits; Sec. VI chunks kept unit-aligned instead of gathered
+    # densely), on the same field, outside the timed step
+    formats = []
+    if args.merge == "scan" and 9 <= args.chunk_log2 <= 12:
+        for W in (32, 16, 8):
+            for layout in (0, 1):
+                prm = dict(params, word_bits=W, layout=layout)
+                p2 = huff.Pipeline(n, nbins, prm)
+                p2.run(sym)
+                for _ in range(2):
+                    p2.run(sym, stages=("encode",))
+                ts = []
+                for _ in range(8):
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    p2.run(sym, stages=("encode",))
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ts.append(e0.elapsed_time(e1) * 1e3)
+                st2 = p2.status()
+                if st2 != 0:
+                    raise RuntimeError(f"format W={W} layout={layout}: device status {huff.STATUS.get(st2, st2)}")
+                tb2 = int(p2.total_bits.item())
+                formats.append({"word_bits": W, "layout": "chunk_aligned" if layout else "dense",
+                                "encode_us_mean": round(statistics.mean(ts), 2), "encode_us_best": round(min(ts), 2),
+                                "stream_bytes": (tb2 + W - 1) // W * W // 8,
+                                "input_GBps": round(in_bytes / (statistics.mean(ts) * 1e-6) / 1e9, 1)})
+                del p2
+
     # end to end through the binding from pinned host memory: every step copies
     # its input in and its stream and offsets out.  Two buffer sets and two copy
     # streams let step k + 1's input copy overlap step k's compute and read-back.
@@ -487,6 +518,7 @@ def run_ours(args, world, rank, local):
         "cpu_baseline": cpu,
         "clocks": clk,
         "decode": dec,
+        "format_ablation": formats,
     }
     return line
 

@@ -101,7 +101,23 @@ typedef struct {
                               autotuner of the batched form picks CTAs per SM); any value is
                               accepted and ignored                                            */
     int32_t merge;         /* HUFF_MERGE_*                                                    */
+    int32_t word_bits;     /* W, the typed unit of the stream (Sec. IV-C: uint{8,16,32} data
+                              cells): 8, 16 or 32 (0 = 32).  The stream is an array of W-bit
+                              units, bit W-1 of unit 0 first; W also replaces 32 in the r
+                              rule (huff_reduce_factor(beta, W)).  8 and 16 need the scan
+                              encoder (merge AUTO or SCAN)                                    */
+    int32_t layout;        /* HUFF_LAYOUT_*                                                   */
 } huff_params;
+
+enum {
+    HUFF_LAYOUT_DENSE = 0,          /* one bit-contiguous stream; offsets count bits           */
+    HUFF_LAYOUT_CHUNK_ALIGNED = 1   /* the chunks before the optional dense gathering (Sec. VI):
+                                       every chunk of 2^M symbols starts at a W-bit unit, its
+                                       last unit zero-padded; offsets count units.  Needs the
+                                       scan encoder and M within one encoder sub-tile and at
+                                       least one warp's symbols: 10..13 for u8, 9..12 for u16,
+                                       8..11 for u32                                          */
+};
 
 enum {
     HUFF_MERGE_AUTO = 0,     /* = HUFF_MERGE_SCAN                                                */
@@ -114,7 +130,8 @@ enum {
                                 M - r <= 10, and a workspace sized with these parameters      */
 };
 
-/* Fills *p with the defaults (M = 10, r = auto, block = 0, merge = auto). */
+/* Fills *p with the defaults (M = 10, r = auto, block = 0, merge = auto, W = 32,
+   dense layout). */
 void huff_default_params(huff_params *p);
 
 /*
@@ -130,6 +147,11 @@ size_t huff_codebook_bytes(uint32_t nbins);
 
 /* Bytes of output (uint32 words) that always suffice: ceil(n * max_len / 32). */
 uint64_t huff_max_output_words(uint64_t n, uint32_t max_len);
+
+/* Units of W = p->word_bits bits that always suffice for the stream of n
+ * symbols in p's format: ceil(n * max_len / W), plus one unit per chunk for
+ * the padding of the chunk-aligned layout (p = NULL: defaults). */
+uint64_t huff_max_output_units(uint64_t n, uint32_t max_len, const huff_params *p);
 
 /*
  * Bytes of device workspace one histogram/codebook/encode sequence needs for
@@ -172,11 +194,16 @@ huff_status huff_build_codebook(const uint32_t *d_hist, uint32_t nbins, void *d_
  *   d_sym              n symbols (< 2^32) of `dtype`
  *   d_codebook         a codebook built for the same alphabet
  *   nbins              its alphabet size (checked against the codebook on the device)
- *   p                  tunables (NULL = defaults); they never change the output
- *   d_out              out_capacity_words uint32; receives ceil(total_bits/32) words
- *   d_chunk_bit_offset ceil(n / 2^M) + 1 uint64: bit position of symbol c*2^M;
- *                      the last entry is total_bits
- *   d_total_bits       one uint64
+ *   p                  tunables (NULL = defaults); chunk_log2, word_bits and layout
+ *                      choose the format, the others never change the output
+ *   d_out              4-byte aligned; out_capacity_words units of W bits (uint32
+ *                      words for the default W = 32); receives ceil(total_bits/W)
+ *                      units.  With W < 32 the allocation must extend to a whole
+ *                      number of 32-bit words (the decoder reads whole words)
+ *   d_chunk_bit_offset ceil(n / 2^M) + 1 uint64: dense layout, bit position of
+ *                      symbol c*2^M and last entry total_bits; chunk-aligned
+ *                      layout, unit index of chunk c and last entry the units
+ *   d_total_bits       one uint64: the stream's bits (chunk-aligned: with padding)
  * A symbol >= nbins or without codeword records an error; so does a stream
  * longer than the capacity (nothing is written past it).
  */
@@ -207,6 +234,18 @@ huff_status huff_encode(const void *d_sym, uint64_t n, huff_dtype dtype, const v
 huff_status huff_decode(const uint32_t *d_in, uint64_t total_bits, const uint64_t *d_chunk_bit_offset,
                         int chunk_log2, uint64_t n, huff_dtype dtype, const void *d_codebook,
                         uint32_t nbins, void *d_out, void *d_ws, void *stream);
+
+/*
+ * huff_decode for any format huff_encode writes: p's chunk_log2, word_bits
+ * and layout must be those of the encode (p = NULL: defaults, the same as
+ * huff_decode).  d_in holds the units (4-byte aligned, readable to a whole
+ * number of 32-bit words); d_chunk_bit_offset and total_bits are the
+ * encode's, in its units.  In the chunk-aligned layout a chunk's codes must
+ * end within the last unit before the next chunk's offset.
+ */
+huff_status huff_decode_ex(const void *d_in, uint64_t total_bits, const uint64_t *d_chunk_bit_offset,
+                           const huff_params *p, uint64_t n, huff_dtype dtype, const void *d_codebook,
+                           uint32_t nbins, void *d_out, void *d_ws, void *stream);
 
 /*
  * Encode without any device allocation by the library or the caller's

@@ -37,7 +37,12 @@ class HuffError(RuntimeError):
 
 class huff_params(ctypes.Structure):
     _fields_ = [("chunk_log2", ctypes.c_int32), ("reduce_log2", ctypes.c_int32),
-                ("block_threads", ctypes.c_int32), ("merge", ctypes.c_int32)]
+                ("block_threads", ctypes.c_int32), ("merge", ctypes.c_int32),
+                ("word_bits", ctypes.c_int32), ("layout", ctypes.c_int32)]
+
+
+HUFF_LAYOUT_DENSE = 0
+HUFF_LAYOUT_CHUNK_ALIGNED = 1
 
 
 class huff_field(ctypes.Structure):
@@ -102,12 +107,14 @@ def lib() -> ctypes.CDLL:
             "huff_reduce_factor": (i32, [ctypes.c_double, i32]),
             "huff_codebook_bytes": (sz, [u32]),
             "huff_max_output_words": (u64, [u64, u32]),
+            "huff_max_output_units": (u64, [u64, u32, P]),
             "huff_workspace_bytes": (sz, [u64, u32, P]),
             "huff_workspace_init": (i32, [vp, vp]),
             "huff_histogram": (i32, [vp, u64, i32, u32, vp, vp, vp]),
             "huff_build_codebook": (i32, [vp, u32, vp, vp, vp]),
             "huff_encode": (i32, [vp, u64, i32, vp, u32, P, vp, u64, vp, vp, vp, vp]),
             "huff_decode": (i32, [vp, u64, vp, i32, u64, i32, vp, u32, vp, vp, vp]),
+            "huff_decode_ex": (i32, [vp, u64, vp, P, u64, i32, vp, u32, vp, vp, vp]),
             "huff_encode_noalloc": (i32, [vp, u64, i32, vp, u32, P, vp, u64, vp, vp, vp, vp]),
             "huff_encode_fault_test": (i32, [vp, u64, i32, vp, u32, vp, u64, vp, vp, u32, vp, vp]),
             "huff_get_status": (i32, [vp, vp]),
@@ -208,6 +215,10 @@ def huff_max_output_words(n: int, max_len: int) -> int:
     return lib().huff_max_output_words(n, max_len)
 
 
+def huff_max_output_units(n: int, max_len: int, params=None) -> int:
+    return lib().huff_max_output_units(n, max_len, ctypes.byref(_params(params)))
+
+
 def huff_workspace_bytes(n: int, nbins: int, params=None) -> int:
     return lib().huff_workspace_bytes(n, nbins, ctypes.byref(_params(params)))
 
@@ -267,6 +278,13 @@ def huff_decode(stream_words, total_bits: int, offsets, chunk_log2: int, n: int,
                              nbins, _ptr(out), _ptr(ws), _stream(stream)), "huff_decode")
 
 
+def huff_decode_ex(stream_units, total_bits: int, offsets, params, n: int, dtype: int, codebook, nbins: int,
+                   out, ws, stream=None) -> None:
+    p = _params(params)
+    _check(lib().huff_decode_ex(_ptr(stream_units), total_bits, _ptr(offsets), ctypes.byref(p), n, dtype,
+                                _ptr(codebook), nbins, _ptr(out), _ptr(ws), _stream(stream)), "huff_decode_ex")
+
+
 def huff_get_status(ws, stream=None) -> int:
     return lib().huff_get_status(_ptr(ws), _stream(stream))
 
@@ -320,8 +338,10 @@ class Pipeline:
         self.hist = torch.empty(nbins, dtype=torch.int32, device=self.device)
         self.codebook = torch.empty(huff_codebook_bytes(nbins), dtype=torch.uint8, device=self.device)
         self.ws = torch.zeros(huff_workspace_bytes(max_n, nbins, self.params), dtype=torch.uint8, device=self.device)
-        cap = max(1, huff_max_output_words(max_n, max_len_bound))
-        self.out = torch.empty(cap, dtype=torch.int32, device=self.device)
+        # the stream's units (W = params.word_bits bits each), in whole 32-bit words
+        W = self.params.word_bits or 32
+        self.cap_units = max(1, huff_max_output_units(max_n, max_len_bound, self.params))
+        self.out = torch.empty((self.cap_units * W + 31) // 32, dtype=torch.int32, device=self.device)
         nch = (max_n + (1 << self.params.chunk_log2) - 1) >> self.params.chunk_log2
         self.offsets = torch.empty(nch + 1, dtype=torch.int64, device=self.device)
         self.total_bits = torch.zeros(1, dtype=torch.int64, device=self.device)
@@ -337,7 +357,7 @@ class Pipeline:
             huff_build_codebook(self.hist, self.nbins, self.codebook, self.ws, stream)
         if "encode" in stages:
             huff_encode(sym, self.codebook, self.nbins, self.out, self.offsets, self.total_bits, self.ws,
-                        self.params, stream)
+                        self.params, stream, capacity_words=self.cap_units)
 
     def status(self, stream=None) -> int:
         return huff_get_status(self.ws, stream)

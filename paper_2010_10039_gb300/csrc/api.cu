@@ -83,6 +83,8 @@ void huff_default_params(huff_params *p) {
     p->reduce_log2 = -1;
     p->block_threads = 0;
     p->merge = HUFF_MERGE_AUTO;
+    p->word_bits = 32;
+    p->layout = HUFF_LAYOUT_DENSE;
 }
 
 int huff_reduce_factor(double avg_bits, int word_bits) {
@@ -101,6 +103,17 @@ size_t huff_codebook_bytes(uint32_t nbins) {
 
 uint64_t huff_max_output_words(uint64_t n, uint32_t max_len) {
     return (n * (uint64_t)max_len + 31) / 32;
+}
+
+uint64_t huff_max_output_units(uint64_t n, uint32_t max_len, const huff_params *p) {
+    huff_params prm;
+    huff_default_params(&prm);
+    if (p) prm = *p;
+    const uint64_t W = prm.word_bits == 8 ? 8 : prm.word_bits == 16 ? 16 : 32;
+    uint64_t u = (n * (uint64_t)max_len + W - 1) / W;
+    if (prm.layout == HUFF_LAYOUT_CHUNK_ALIGNED && prm.chunk_log2 >= 0 && prm.chunk_log2 <= 40)
+        u += (n + (1ull << prm.chunk_log2) - 1) >> prm.chunk_log2;
+    return u;
 }
 
 size_t huff_workspace_bytes(uint64_t n, uint32_t nbins, const huff_params *p) {
@@ -149,6 +162,8 @@ huff_status huff_encode(const void *d_sym, uint64_t n, huff_dtype dtype, const v
     if (prm.chunk_log2 < 4 || prm.chunk_log2 > 30 || prm.chunk_log2 < encode_run_log2(dtype)) return HUFF_ERR_INVALID_ARG;
     if (prm.reduce_log2 != -1 && (prm.reduce_log2 < 0 || prm.reduce_log2 > prm.chunk_log2)) return HUFF_ERR_INVALID_ARG;
     if (prm.merge < HUFF_MERGE_AUTO || prm.merge > HUFF_MERGE_SHUFFLE) return HUFF_ERR_INVALID_ARG;
+    uint32_t fmt = 0;
+    if (encode_format_of(prm, dtype, &fmt) != HUFF_OK) return HUFF_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     if (n == 0) {
         if (cudaMemsetAsync(d_chunk_bit_offset, 0, 8, st) != cudaSuccess) return HUFF_ERR_CUDA;
@@ -159,8 +174,8 @@ huff_status huff_encode(const void *d_sym, uint64_t n, huff_dtype dtype, const v
         return encode_shuffle_launch(d_sym, n, dtype, d_codebook, nbins, prm.chunk_log2, prm.reduce_log2, 48, d_out,
                                      out_capacity_words, d_chunk_bit_offset, d_total_bits, scratch_of(d_ws),
                                      status_of(d_ws), st);
-    return encode_launch(d_sym, n, dtype, d_codebook, nbins, prm.chunk_log2, prm.reduce_log2, d_out, out_capacity_words,
-                         d_chunk_bit_offset, d_total_bits, scratch_of(d_ws), status_of(d_ws), st);
+    return encode_launch(d_sym, n, dtype, d_codebook, nbins, prm.chunk_log2, prm.reduce_log2, fmt, d_out,
+                         out_capacity_words, d_chunk_bit_offset, d_total_bits, scratch_of(d_ws), status_of(d_ws), st);
 }
 
 huff_status huff_encode_fault_test(const void *d_sym, uint64_t n, huff_dtype dtype, const void *d_codebook,
@@ -176,22 +191,44 @@ huff_status huff_encode_fault_test(const void *d_sym, uint64_t n, huff_dtype dty
         return HUFF_ERR_INVALID_ARG;
     huff_params prm;
     huff_default_params(&prm);
-    return encode_launch_ex(d_sym, n, dtype, d_codebook, nbins, prm.chunk_log2, prm.reduce_log2, d_out,
+    return encode_launch_ex(d_sym, n, dtype, d_codebook, nbins, prm.chunk_log2, prm.reduce_log2, 0u, d_out,
                             out_capacity_words, d_chunk_bit_offset, d_total_bits, scratch_of(d_ws), status_of(d_ws),
                             (cudaStream_t)stream, 1u, poll_limit);
+}
+
+static huff_status decode_checked(const void *d_in, uint64_t total_bits, const uint64_t *d_chunk_bit_offset,
+                                  const huff_params &prm, uint64_t n, huff_dtype dtype, const void *d_codebook,
+                                  uint32_t nbins, void *d_out, void *d_ws, void *stream) {
+    if (!dtype_ok(dtype) || !nbins_ok(dtype, nbins) || !d_codebook || !d_ws || (n && (!d_in || !d_out || !d_chunk_bit_offset)))
+        return HUFF_ERR_INVALID_ARG;
+    if (prm.chunk_log2 < 0 || prm.chunk_log2 > 30) return HUFF_ERR_INVALID_ARG;
+    if (!elem_aligned(d_out, dtype) || ((uintptr_t)d_in & 3) != 0 || ((uintptr_t)d_chunk_bit_offset & 7) != 0 ||
+        ((uintptr_t)d_codebook & 15) != 0)
+        return HUFF_ERR_INVALID_ARG;
+    const int W = prm.word_bits == 0 ? 32 : prm.word_bits;
+    if (W != 8 && W != 16 && W != 32) return HUFF_ERR_INVALID_ARG;
+    if (prm.layout != HUFF_LAYOUT_DENSE && prm.layout != HUFF_LAYOUT_CHUNK_ALIGNED) return HUFF_ERR_INVALID_ARG;
+    const uint32_t fmt = (W == 32 ? 0u : W == 16 ? 1u : 2u) | (prm.layout == HUFF_LAYOUT_CHUNK_ALIGNED ? 0x100u : 0u);
+    return decode_launch(d_in, total_bits, d_chunk_bit_offset, prm.chunk_log2, fmt, n, dtype, d_codebook, nbins,
+                         d_out, status_of(d_ws), (cudaStream_t)stream);
 }
 
 huff_status huff_decode(const uint32_t *d_in, uint64_t total_bits, const uint64_t *d_chunk_bit_offset,
                         int chunk_log2, uint64_t n, huff_dtype dtype, const void *d_codebook, uint32_t nbins,
                         void *d_out, void *d_ws, void *stream) {
-    if (!dtype_ok(dtype) || !nbins_ok(dtype, nbins) || !d_codebook || !d_ws || (n && (!d_in || !d_out || !d_chunk_bit_offset)))
-        return HUFF_ERR_INVALID_ARG;
-    if (chunk_log2 < 0 || chunk_log2 > 30) return HUFF_ERR_INVALID_ARG;
-    if (!elem_aligned(d_out, dtype) || ((uintptr_t)d_in & 3) != 0 || ((uintptr_t)d_chunk_bit_offset & 7) != 0 ||
-        ((uintptr_t)d_codebook & 15) != 0)
-        return HUFF_ERR_INVALID_ARG;
-    return decode_launch(d_in, total_bits, d_chunk_bit_offset, chunk_log2, n, dtype, d_codebook, nbins, d_out,
-                         status_of(d_ws), (cudaStream_t)stream);
+    huff_params prm;
+    huff_default_params(&prm);
+    prm.chunk_log2 = chunk_log2;
+    return decode_checked(d_in, total_bits, d_chunk_bit_offset, prm, n, dtype, d_codebook, nbins, d_out, d_ws, stream);
+}
+
+huff_status huff_decode_ex(const void *d_in, uint64_t total_bits, const uint64_t *d_chunk_bit_offset,
+                           const huff_params *p, uint64_t n, huff_dtype dtype, const void *d_codebook,
+                           uint32_t nbins, void *d_out, void *d_ws, void *stream) {
+    huff_params prm;
+    huff_default_params(&prm);
+    if (p) prm = *p;
+    return decode_checked(d_in, total_bits, d_chunk_bit_offset, prm, n, dtype, d_codebook, nbins, d_out, d_ws, stream);
 }
 
 huff_status huff_get_status(const void *d_ws, void *stream) {

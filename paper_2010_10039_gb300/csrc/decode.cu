@@ -44,7 +44,7 @@ __shared__ uint16_t dec_lpfx[kL2Entries / 2];   // level-1 window of each number
 __shared__ uint32_t dec_pair[1u << kLutBits];
 
 struct DecArgs {
-    const uint32_t *in;
+    const uint32_t *in;   // whole 32-bit words of the stream's units
     uint64_t total_bits;
     uint64_t in_words;
     const uint64_t *offs;
@@ -57,17 +57,22 @@ struct DecArgs {
     int vec_out;          // out is 16-byte aligned and a chunk is a whole number of 16-byte runs
     int pair_out;         // out is 8-byte aligned and a chunk is a whole number of 8-byte runs
     uint32_t *status;
+    uint32_t perm;        // byte order of a loaded word into stream order: identity for 32-bit
+                          // units, halves swapped for 16-bit, bytes reversed for 8-bit
+    uint32_t off_shift;   // chunk offsets count units of 2^off_shift bits (0: bits)
+    uint32_t unit_mask;   // chunk-aligned layout: unit bits - 1 (a chunk ends within its last unit); 0: dense
 };
 
-__device__ __forceinline__ uint32_t ld_word(const uint32_t *in, uint64_t nwords, uint64_t w) {
-    return w < nwords ? __ldg(in + w) : 0u;
+__device__ __forceinline__ uint32_t ld_word(const uint32_t *in, uint64_t nwords, uint64_t w, uint32_t perm) {
+    return w < nwords ? __byte_perm(__ldg(in + w), 0u, perm) : 0u;
 }
 
 // The stream's bits [p, p + 64), MSB first (zeros past the end).
-__device__ __forceinline__ uint64_t window64(const uint32_t *in, uint64_t nwords, uint64_t p) {
+__device__ __forceinline__ uint64_t window64(const uint32_t *in, uint64_t nwords, uint64_t p, uint32_t perm) {
     const uint64_t w = p >> 5;
     const uint32_t sh = p & 31;
-    const uint64_t a = ld_word(in, nwords, w), b = ld_word(in, nwords, w + 1), c = ld_word(in, nwords, w + 2);
+    const uint64_t a = ld_word(in, nwords, w, perm), b = ld_word(in, nwords, w + 1, perm),
+                   c = ld_word(in, nwords, w + 2, perm);
     const uint64_t hi = (a << 32) | b;
     return sh ? (hi << sh) | (c >> (32 - sh)) : hi;
 }
@@ -107,7 +112,8 @@ __device__ __forceinline__ void decode_chunk(const DecArgs &a, const uint32_t *g
     const uint32_t *cin = a.in + cw0;
     const uint64_t left = a.in_words > cw0 ? a.in_words - cw0 : 0;
     const uint32_t lim = left < 0xFFFFFFFFull ? (uint32_t)left : 0xFFFFFFFFu;
-    auto word = [&](uint32_t k) { return k < lim ? __ldg(cin + k) : 0u; };
+    const uint32_t perm = a.perm;
+    auto word = [&](uint32_t k) { return k < lim ? __byte_perm(__ldg(cin + k), 0u, perm) : 0u; };
     uint32_t hi, lo, nb, wn, nxt;
     auto start = [&](uint64_t p) {
         wn = (uint32_t)((p >> 5) - cw0);
@@ -146,7 +152,7 @@ __device__ __forceinline__ void decode_chunk(const DecArgs &a, const uint32_t *g
             // the buffer when it holds max_len bits, else on a fresh window
             uint32_t r = 0;
             if (e == 0) {
-                const uint64_t win = max_len <= nb ? ((uint64_t)hi << 32 | lo) : window64(a.in, a.in_words, pos());
+                const uint64_t win = max_len <= nb ? ((uint64_t)hi << 32 | lo) : window64(a.in, a.in_words, pos(), a.perm);
                 r = decode_long(win, L, max_len, gsyms);
             }
             if (r == 0) { ok = false; return; }
@@ -237,7 +243,11 @@ __device__ __forceinline__ void decode_chunk(const DecArgs &a, const uint32_t *g
         next(s);
         if (ok) out[i] = (Sym)s;
     }
-    if (!ok || pos() != pend) set_error(a.status, HUFF_ERR_INVALID_ARG);
+    // dense: the chunk ends exactly at the next offset; chunk-aligned: within
+    // the unit before it (the rest of that unit is padding)
+    const uint64_t pe = pos();
+    if (!ok || pe > pend || ((pe + a.unit_mask) & ~(uint64_t)a.unit_mask) != pend)
+        set_error(a.status, HUFF_ERR_INVALID_ARG);
 }
 
 template <int W>
@@ -350,17 +360,22 @@ __global__ void __launch_bounds__(kDecThreads) decode_kernel(DecArgs a) {
     for (uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; c < a.nchunks; c += stride) {
         const uint64_t i0 = c << a.chunk_log2;
         const uint64_t i1 = i0 + (1ull << a.chunk_log2) < a.n ? i0 + (1ull << a.chunk_log2) : a.n;
-        decode_chunk<W>(a, sorted_syms, pair, L, max_len, i0, i1, a.offs[c], a.offs[c + 1]);
+        decode_chunk<W>(a, sorted_syms, pair, L, max_len, i0, i1, a.offs[c] << a.off_shift,
+                        a.offs[c + 1] << a.off_shift);
     }
 }
 
-huff_status decode_launch(const uint32_t *d_in, uint64_t total_bits, const uint64_t *d_offs, int chunk_log2,
-                          uint64_t n, huff_dtype dtype, const void *d_codebook, uint32_t nbins, void *d_out,
-                          uint32_t *status, cudaStream_t st) {
+huff_status decode_launch(const void *d_in, uint64_t total_bits, const uint64_t *d_offs, int chunk_log2,
+                          uint32_t format, uint64_t n, huff_dtype dtype, const void *d_codebook, uint32_t nbins,
+                          void *d_out, uint32_t *status, cudaStream_t st) {
     DecArgs a;
-    a.in = d_in;
+    a.in = static_cast<const uint32_t *>(d_in);
     a.total_bits = total_bits;
     a.in_words = (total_bits + 31) / 32;
+    const uint32_t wlog = fmt_wlog(format);
+    a.perm = wlog == 5 ? 0x3210u : wlog == 4 ? 0x1032u : 0x0123u;
+    a.off_shift = fmt_chunk_aligned(format) ? wlog : 0u;
+    a.unit_mask = fmt_chunk_aligned(format) ? (1u << wlog) - 1 : 0u;
     a.offs = d_offs;
     a.chunk_log2 = chunk_log2;
     a.n = n;

@@ -40,9 +40,9 @@ static uint32_t pow2_at_least(uint32_t x) {
 
 template <typename Sym>
 static huff_status launch_encode(const void *d_sym, uint64_t n, const void *d_codebook, uint32_t nbins_host,
-                                 int chunk_log2, int reduce_log2, uint32_t *d_out, uint64_t cap, uint64_t *d_offs,
-                                 uint64_t *d_total, uint8_t *scratch, uint32_t *status, cudaStream_t st,
-                                 uint32_t id_offset, uint32_t spin_limit) {
+                                 int chunk_log2, int reduce_log2, uint32_t format, uint32_t *d_out, uint64_t cap,
+                                 uint64_t *d_offs, uint64_t *d_total, uint8_t *scratch, uint32_t *status,
+                                 cudaStream_t st, uint32_t id_offset, uint32_t spin_limit) {
     constexpr uint32_t SUB = enc_sub_syms<Sym>();
     EncArgs a{};
     a.one.sym = static_cast<const uint8_t *>(d_sym);
@@ -57,6 +57,7 @@ static huff_status launch_encode(const void *d_sym, uint64_t n, const void *d_co
     a.one.nbins = nbins_host;
     a.one.chunk_log2 = chunk_log2;
     a.one.aligned = ((uintptr_t)d_sym & 15) == 0;
+    a.one.format = format;
     a.fields = nullptr;
     a.conf = nullptr;
     a.nfields = 1;
@@ -77,7 +78,8 @@ static huff_status launch_encode(const void *d_sym, uint64_t n, const void *d_co
         a.etab = etab;
     }
     const size_t smem = enc_smem_bytes<Sym>(gtab, a.tslots, 0);
-    void (*kern)(EncArgs) = gtab ? encode_kernel<Sym, true, false> : encode_kernel<Sym, false, false>;
+    void (*kern)(EncArgs) = fmt_chunk_aligned(format) ? encode_kernel_aligned<Sym>(gtab)
+                            : gtab ? encode_kernel<Sym, true, false> : encode_kernel<Sym, false, false>;
     if (!allow_dynamic_smem((const void *)kern, smem))
         return HUFF_ERR_CUDA;
     int occ = 0;
@@ -91,22 +93,40 @@ static huff_status launch_encode(const void *d_sym, uint64_t n, const void *d_co
 }
 
 huff_status encode_launch_ex(const void *d_sym, uint64_t n, huff_dtype dtype, const void *d_codebook, uint32_t nbins,
-                             int chunk_log2, int reduce_log2, uint32_t *d_out, uint64_t cap, uint64_t *d_offs,
-                             uint64_t *d_total, uint8_t *scratch, uint32_t *status, cudaStream_t st, uint32_t id_offset,
-                             uint32_t spin_limit) {
+                             int chunk_log2, int reduce_log2, uint32_t format, uint32_t *d_out, uint64_t cap,
+                             uint64_t *d_offs, uint64_t *d_total, uint8_t *scratch, uint32_t *status, cudaStream_t st,
+                             uint32_t id_offset, uint32_t spin_limit) {
     switch (dtype) {
-        case HUFF_U8: return launch_encode<uint8_t>(d_sym, n, d_codebook, nbins, chunk_log2, reduce_log2, d_out, cap, d_offs, d_total, scratch, status, st, id_offset, spin_limit);
-        case HUFF_U16: return launch_encode<uint16_t>(d_sym, n, d_codebook, nbins, chunk_log2, reduce_log2, d_out, cap, d_offs, d_total, scratch, status, st, id_offset, spin_limit);
-        case HUFF_U32: return launch_encode<uint32_t>(d_sym, n, d_codebook, nbins, chunk_log2, reduce_log2, d_out, cap, d_offs, d_total, scratch, status, st, id_offset, spin_limit);
+        case HUFF_U8: return launch_encode<uint8_t>(d_sym, n, d_codebook, nbins, chunk_log2, reduce_log2, format, d_out, cap, d_offs, d_total, scratch, status, st, id_offset, spin_limit);
+        case HUFF_U16: return launch_encode<uint16_t>(d_sym, n, d_codebook, nbins, chunk_log2, reduce_log2, format, d_out, cap, d_offs, d_total, scratch, status, st, id_offset, spin_limit);
+        case HUFF_U32: return launch_encode<uint32_t>(d_sym, n, d_codebook, nbins, chunk_log2, reduce_log2, format, d_out, cap, d_offs, d_total, scratch, status, st, id_offset, spin_limit);
     }
     return HUFF_ERR_INVALID_ARG;
 }
 
 huff_status encode_launch(const void *d_sym, uint64_t n, huff_dtype dtype, const void *d_codebook, uint32_t nbins,
-                          int chunk_log2, int reduce_log2, uint32_t *d_out, uint64_t cap, uint64_t *d_offs,
-                          uint64_t *d_total, uint8_t *scratch, uint32_t *status, cudaStream_t st) {
-    return encode_launch_ex(d_sym, n, dtype, d_codebook, nbins, chunk_log2, reduce_log2, d_out, cap, d_offs, d_total,
-                            scratch, status, st, 0u, 0u);
+                          int chunk_log2, int reduce_log2, uint32_t format, uint32_t *d_out, uint64_t cap,
+                          uint64_t *d_offs, uint64_t *d_total, uint8_t *scratch, uint32_t *status, cudaStream_t st) {
+    return encode_launch_ex(d_sym, n, dtype, d_codebook, nbins, chunk_log2, reduce_log2, format, d_out, cap, d_offs,
+                            d_total, scratch, status, st, 0u, 0u);
+}
+
+huff_status encode_format_of(const huff_params &p, huff_dtype dtype, uint32_t *fmt) {
+    const int W = p.word_bits == 0 ? 32 : p.word_bits;
+    if (W != 8 && W != 16 && W != 32) return HUFF_ERR_INVALID_ARG;
+    if (p.layout != HUFF_LAYOUT_DENSE && p.layout != HUFF_LAYOUT_CHUNK_ALIGNED) return HUFF_ERR_INVALID_ARG;
+    const bool aligned = p.layout == HUFF_LAYOUT_CHUNK_ALIGNED;
+    if ((W != 32 || aligned) && p.merge == HUFF_MERGE_SHUFFLE) return HUFF_ERR_INVALID_ARG;
+    if (aligned) {
+        // chunk boundaries must fall on warp boundaries of a sub-tile: the
+        // padding is added to the warp totals of the tile scan
+        int sub_log2 = 0;
+        while ((1u << (sub_log2 + 1)) <= encode_sub_symbols(dtype)) sub_log2++;
+        const int warp_log2 = sub_log2 - 3;                     // 8 merge warps per sub-tile
+        if (p.chunk_log2 < warp_log2 || p.chunk_log2 > sub_log2) return HUFF_ERR_INVALID_ARG;
+    }
+    *fmt = (W == 32 ? 0u : W == 16 ? 1u : 2u) | (aligned ? 0x100u : 0u);
+    return HUFF_OK;
 }
 
 uint32_t encode_sub_symbols(huff_dtype dtype) {

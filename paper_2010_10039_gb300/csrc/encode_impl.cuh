@@ -539,7 +539,7 @@ __device__ __forceinline__ void load_table(Entry *tab, uint32_t tslots, const En
 // The 8 merge warps: reduce-merge every tile into the bit ring, publish its
 // aggregate and hand it to the look-back and write-out warps.  R2 = r:
 // 2^r codewords per register.
-template <typename Sym, typename Entry, int TAB, int R2, bool BATCH>
+template <typename Sym, typename Entry, int TAB, int R2, bool BATCH, bool CALIGN>
 __device__ void merge_warps(const EncArgs &a, const EncField *fields, const uint32_t *tbase, uint8_t *stage,
                             uint32_t *ring, Entry *tab, uint32_t total, uint32_t nsub1, uint32_t max_len1,
                             EncShared &S) {
@@ -581,6 +581,14 @@ __device__ void merge_warps(const EncArgs &a, const EncField *fields, const uint
     merge_sync();
 
     uint32_t it = 0, t = 0, base = 0, cur_f = 0xFFFFFFFFu;
+    // chunk-aligned layout (CALIGN: single-field launches only): a chunk is a
+    // group of pad_group = 2^M / (warp's symbols) consecutive merge warps,
+    // 1..8 (checked on the host)
+    constexpr uint32_t kWarpLog2 = 5 + 1 + (sizeof(Sym) == 1 ? 4 : sizeof(Sym) == 2 ? 3 : 2);
+    static_assert((1u << kWarpLog2) == 32u * kEncRPT * VecOf<Sym>::N, "warp symbols");
+    static_assert(!(CALIGN && BATCH), "the batched form writes the dense layout");
+    const uint32_t pad_group = CALIGN ? 1u << (a.one.chunk_log2 - kWarpLog2) : 1u;
+    const uint32_t pad_mask = (1u << fmt_wlog(a.one.format)) - 1;
     for (;; t++) {
         const uint32_t g = stage_tile[it % kEncStages];
         const uint32_t f = stage_field[it % kEncStages];
@@ -695,7 +703,15 @@ __device__ void merge_warps(const EncArgs &a, const EncField *fields, const uint
             }
             // exclusive prefix of the 8 warp totals, by shuffles
             constexpr int NW = kEncThreads / 32;
-            const uint32_t wt = lane < NW ? ws[lane] : 0u;
+            uint32_t wt = lane < NW ? ws[lane] : 0u;
+            if constexpr (CALIGN) {
+                // the last warp of each chunk carries the padding up to the
+                // next unit boundary; sub-tiles start at unit boundaries, so
+                // the padding depends only on the chunk's own length
+                uint32_t gs = wt;
+                for (uint32_t o = 1; o < pad_group; o <<= 1) gs += __shfl_xor_sync(0xFFFFFFFFu, gs, o);
+                if ((lane & (pad_group - 1)) == pad_group - 1) wt += ((gs + pad_mask) & ~pad_mask) - gs;
+            }
             uint32_t wi = wt;
 #pragma unroll
             for (int o = 1; o < NW; o <<= 1) {
@@ -785,7 +801,7 @@ static __device__ void lookback_loop(const EncArgs &a, const EncField *fields, u
                 S.slot[sl].G = G;
                 S.slot[sl].prev = prev;
                 if (j == F.ntiles - 1) {
-                    F.offs[F.nchunks] = G + L;
+                    F.offs[F.nchunks] = fmt_chunk_aligned(F.format) ? (G + L) >> fmt_wlog(F.format) : G + L;
                     *F.total_bits = G + L;
                 }
             }
@@ -797,6 +813,75 @@ static __device__ void lookback_loop(const EncArgs &a, const EncField *fields, u
 }
 
 // ---------------------------------------------------------------- write-out warp
+
+// Copies one tile's nw stream words from the ring to outw (the stream's word
+// w0 on): word i is the funnel shift of ring words wb + i and wb + i + 1 (one
+// SHF, which also covers sh = 0); the first word, when the tile starts
+// mid-word, is completed with the previous tile's last bits.  A block of 128
+// words that is whole, inside the capacity, does not hold the shared first
+// word and does not hold a masked last word takes no per-word checks (the
+// test is warp-uniform).  Four independent words per lane per step, four
+// coalesced stores.  TYPED: units of 8 or 16 bits, so each word is permuted
+// into stream order (perm) and the capacity and the stream's last word are
+// counted in bytes (narrow stores for a last word only partly inside).
+// Returns whether a word fell outside the capacity (it is not written).
+template <bool TYPED, uint32_t RMASK>
+__device__ __forceinline__ bool copy_tile_words(const uint32_t *ring, uint32_t *outw, uint32_t wb, uint32_t sh,
+                                                uint32_t g31, uint32_t prev, uint32_t nw, bool last,
+                                                uint32_t tail_bits, uint32_t tail_mask, uint64_t room_bytes,
+                                                uint32_t tail_bytes, uint32_t perm, uint32_t lane) {
+    const uint64_t room = room_bytes >> 2;                                   // whole words
+    bool over = false;
+    for (uint32_t b0 = 0; b0 < nw; b0 += 128) {
+        const bool fast = b0 + 128 <= nw && (uint64_t)(b0 + 128) <= room && !(b0 == 0 && g31) &&
+                          !(b0 + 128 == nw && last && tail_bits);
+        uint32_t val[4];
+        if (fast) {
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const uint32_t i = b0 + 32 * k + lane;
+                val[k] = __funnelshift_l(ring[(wb + i + 1) & RMASK], ring[(wb + i) & RMASK], sh);
+                if (TYPED) val[k] = __byte_perm(val[k], 0u, perm);
+            }
+#pragma unroll
+            for (int k = 0; k < 4; k++) outw[b0 + 32 * k + lane] = val[k];
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const uint32_t i = b0 + 32 * k + lane;
+                const uint32_t hi = ring[(wb + i) & RMASK], lo = ring[(wb + i + 1) & RMASK];
+                val[k] = __funnelshift_l(lo, hi, sh);
+                if (i == 0 && g31) val[k] = ((prev & ((1u << g31) - 1)) << (32 - g31)) | (lo >> g31);
+                if (i == nw - 1) val[k] &= tail_mask;
+                if (TYPED) val[k] = __byte_perm(val[k], 0u, perm);
+            }
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const uint32_t i = b0 + 32 * k + lane;
+                if (i < nw) {
+                    if (!TYPED) {
+                        if ((uint64_t)i < room) outw[i] = val[k]; else over = true;
+                    } else {
+                        const uint32_t want = i == nw - 1 ? tail_bytes : 4u;
+                        if (4ull * i + want <= room_bytes) {
+                            if (want == 4) {
+                                outw[i] = val[k];
+                            } else if (want == 2) {
+                                reinterpret_cast<uint16_t *>(outw + i)[0] = (uint16_t)val[k];
+                            } else {
+                                uint8_t *ob = reinterpret_cast<uint8_t *>(outw + i);
+                                for (uint32_t x = 0; x < want; x++) ob[x] = (uint8_t)(val[k] >> (8 * x));
+                            }
+                        } else {
+                            over = true;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    return over;
+}
 
 // Copies each tile from the ring into the dense stream at its offset (the word
 // it shares with the previous tile is completed with the previous tile's last
@@ -820,7 +905,13 @@ __device__ void writeout_loop(const EncField *fields, uint32_t *ring, uint32_t t
         const uint32_t L = S.slot[sl].L, base = S.slot[sl].base, prev = S.slot[sl].prev;
         const bool last = (j == F.ntiles - 1);
         uint32_t *out = F.out;
-        const uint64_t cap = F.cap_words;
+        // capacity and stream end in bytes: units of W = 2^wlog bits (W < 32
+        // stores each 32-bit word's units in stream order: bytes or halves
+        // swapped; a last word only partly inside takes narrow stores)
+        const uint32_t fmt = F.format;
+        const uint32_t wlog = fmt_wlog(fmt);
+        const uint32_t perm = wlog == 5 ? 0x3210u : wlog == 4 ? 0x1032u : 0x0123u;
+        const uint64_t cap_bytes = F.cap_words << (wlog - 3);
         const uint32_t g31 = (uint32_t)(G & 31);
         const uint64_t w0 = G >> 5;
         const uint64_t end_bit = G + L;
@@ -829,47 +920,18 @@ __device__ void writeout_loop(const EncField *fields, uint32_t *ring, uint32_t t
         // the last tile of a field also writes its partial final word, whose
         // ring neighbour may already hold the next tile (of another field)
         const uint32_t tail_mask = (last && tail_bits) ? ~0u << (32 - tail_bits) : ~0u;
-        bool over = false;
+        // bytes of the stream's last word that belong to it (whole units)
+        const uint32_t tail_bytes = (last && tail_bits) ? (((tail_bits + (1u << wlog) - 1) >> wlog) << (wlog - 3)) : 4u;
         // stream word w0 + i holds tile bits [32 i - g31, 32 i - g31 + 32), i.e.
-        // the funnel shift of ring words wb + i and wb + i + 1 (one SHF, which
-        // also covers sh = 0).  A block of 128 words that is whole, inside the
-        // capacity, does not hold the shared first word and does not hold a
-        // masked last word takes no per-word checks (the test is warp-uniform).
-        // Four independent words per lane per step, four coalesced stores.
+        // the funnel shift of ring words wb + i and wb + i + 1
         const uint32_t sh = (32 - g31) & 31;
         const uint32_t wb = base - (g31 ? 1u : 0u);
-        uint32_t *outw = out + w0;
-        const uint64_t room = cap > w0 ? cap - w0 : 0;                // words writable from w0
-        for (uint32_t b0 = 0; b0 < nw; b0 += 128) {
-            const bool fast = b0 + 128 <= nw && (uint64_t)(b0 + 128) <= room && !(b0 == 0 && g31) &&
-                              !(b0 + 128 == nw && last && tail_bits);
-            uint32_t val[4];
-            if (fast) {
-#pragma unroll
-                for (int k = 0; k < 4; k++) {
-                    const uint32_t i = b0 + 32 * k + lane;
-                    val[k] = __funnelshift_l(ring[(wb + i + 1) & RMASK], ring[(wb + i) & RMASK], sh);
-                }
-#pragma unroll
-                for (int k = 0; k < 4; k++) outw[b0 + 32 * k + lane] = val[k];
-            } else {
-#pragma unroll
-                for (int k = 0; k < 4; k++) {
-                    const uint32_t i = b0 + 32 * k + lane;
-                    const uint32_t hi = ring[(wb + i) & RMASK], lo = ring[(wb + i + 1) & RMASK];
-                    val[k] = __funnelshift_l(lo, hi, sh);
-                    if (i == 0 && g31) val[k] = ((prev & ((1u << g31) - 1)) << (32 - g31)) | (lo >> g31);
-                    if (i == nw - 1) val[k] &= tail_mask;
-                }
-#pragma unroll
-                for (int k = 0; k < 4; k++) {
-                    const uint32_t i = b0 + 32 * k + lane;
-                    if (i < nw) {
-                        if ((uint64_t)i < room) outw[i] = val[k]; else over = true;
-                    }
-                }
-            }
-        }
+        const uint64_t room_bytes = cap_bytes > 4 * w0 ? cap_bytes - 4 * w0 : 0;   // bytes writable from w0
+        const bool over = wlog == 5
+            ? copy_tile_words<false, RMASK>(ring, out + w0, wb, sh, g31, prev, nw, last, tail_bits, tail_mask,
+                                            room_bytes, 4u, 0x3210u, lane)
+            : copy_tile_words<true, RMASK>(ring, out + w0, wb, sh, g31, prev, nw, last, tail_bits, tail_mask,
+                                           room_bytes, tail_bytes, perm, lane);
         if (over) set_error(F.status, HUFF_ERR_CAPACITY);
         // chunk offsets were written relative to the tile
         const int M = F.chunk_log2;
@@ -880,7 +942,11 @@ __device__ void writeout_loop(const EncField *fields, uint32_t *ring, uint32_t t
         const uint64_t tend = t0 + TILE < F.n ? t0 + TILE : F.n;
         const uint64_t c_end = (tend + chunk_mask) >> M;
         uint64_t *offs = F.offs;
-        for (uint64_t c = c_first + lane; c < c_end; c += 32) offs[c] += G;
+        if (fmt_chunk_aligned(fmt)) {
+            for (uint64_t c = c_first + lane; c < c_end; c += 32) offs[c] = (offs[c] + G) >> wlog;
+        } else {
+            for (uint64_t c = c_first + lane; c < c_end; c += 32) offs[c] += G;
+        }
         __syncwarp();
         const uint32_t used = (L + 31) / 32;
         for (uint32_t wz = 0; wz < used; wz += 128) {
@@ -914,27 +980,28 @@ __host__ __device__ inline int enc_clamp_r(int r) {
     return r < enc_r_min<Sym>() ? enc_r_min<Sym>() : (r > enc_r_max<Sym>() ? enc_r_max<Sym>() : r);
 }
 
-// Reduction factor rule of Sec. IV-C: floor(log2 beta) + r + 1 = log2(32),
-// beta = total_bits / nsymbols the average codeword length, clamped to
-// [0, 5] like huff_reduce_factor (the caller then applies the register clamp).
-__host__ __device__ inline int enc_rule_r(uint64_t total_bits, uint64_t nsymbols) {
+// Reduction factor rule of Sec. IV-C: floor(log2 beta) + r + 1 = log2(W)
+// (W = 2^wlog, the typed unit), beta = total_bits / nsymbols the average
+// codeword length, clamped to [0, wlog] like huff_reduce_factor (the caller
+// then applies the register clamp).
+__host__ __device__ inline int enc_rule_r(uint64_t total_bits, uint64_t nsymbols, int wlog = 5) {
     // floor(log2(beta)): largest f with nsymbols * 2^f <= total_bits
     int f = 0;
     while (f < 62 && nsymbols && (nsymbols << (f + 1)) <= total_bits && ((nsymbols << (f + 1)) >> (f + 1)) == nsymbols)
         f++;
-    return f > 4 ? 0 : 4 - f;
+    return f > wlog - 1 ? 0 : wlog - 1 - f;
 }
 
-template <typename Sym, typename Entry, int TAB, bool BATCH>
+template <typename Sym, typename Entry, int TAB, bool BATCH, bool CALIGN>
 __device__ void merge_dispatch(int r, const EncArgs &a, const EncField *fields, const uint32_t *tbase,
                                uint8_t *stage, uint32_t *ring, Entry *tab, uint32_t total, uint32_t nsub1,
                                uint32_t max_len1, EncShared &S) {
     switch (r) {
-        case 0: if constexpr (VecOf<Sym>::N <= 4) merge_warps<Sym, Entry, TAB, 0, BATCH>(a, fields, tbase, stage, ring, tab, total, nsub1, max_len1, S); break;
-        case 1: if constexpr (VecOf<Sym>::N <= 4) merge_warps<Sym, Entry, TAB, 1, BATCH>(a, fields, tbase, stage, ring, tab, total, nsub1, max_len1, S); break;
-        case 2: merge_warps<Sym, Entry, TAB, 2, BATCH>(a, fields, tbase, stage, ring, tab, total, nsub1, max_len1, S); break;
-        case 3: if constexpr (VecOf<Sym>::N >= 8) merge_warps<Sym, Entry, TAB, 3, BATCH>(a, fields, tbase, stage, ring, tab, total, nsub1, max_len1, S); break;
-        default: if constexpr (VecOf<Sym>::N >= 16) merge_warps<Sym, Entry, TAB, 4, BATCH>(a, fields, tbase, stage, ring, tab, total, nsub1, max_len1, S); break;
+        case 0: if constexpr (VecOf<Sym>::N <= 4) merge_warps<Sym, Entry, TAB, 0, BATCH, CALIGN>(a, fields, tbase, stage, ring, tab, total, nsub1, max_len1, S); break;
+        case 1: if constexpr (VecOf<Sym>::N <= 4) merge_warps<Sym, Entry, TAB, 1, BATCH, CALIGN>(a, fields, tbase, stage, ring, tab, total, nsub1, max_len1, S); break;
+        case 2: merge_warps<Sym, Entry, TAB, 2, BATCH, CALIGN>(a, fields, tbase, stage, ring, tab, total, nsub1, max_len1, S); break;
+        case 3: if constexpr (VecOf<Sym>::N >= 8) merge_warps<Sym, Entry, TAB, 3, BATCH, CALIGN>(a, fields, tbase, stage, ring, tab, total, nsub1, max_len1, S); break;
+        default: if constexpr (VecOf<Sym>::N >= 16) merge_warps<Sym, Entry, TAB, 4, BATCH, CALIGN>(a, fields, tbase, stage, ring, tab, total, nsub1, max_len1, S); break;
     }
 }
 
@@ -946,7 +1013,7 @@ __host__ __device__ inline size_t enc_smem_bytes(bool gtab, uint32_t tslots, uin
            (nfields_batch ? 4ull * (nfields_batch + 1) : 0);
 }
 
-template <typename Sym, bool GTAB, bool BATCH>
+template <typename Sym, bool GTAB, bool BATCH, bool CALIGN = false>
 __global__ void __launch_bounds__(kEncCtaThreads, sizeof(Sym) == 1 ? 2 : 3) encode_kernel(EncArgs a) {
     extern __shared__ __align__(128) uint8_t smem[];
     constexpr uint32_t RW = ring_words<Sym>();
@@ -979,7 +1046,8 @@ __global__ void __launch_bounds__(kEncCtaThreads, sizeof(Sym) == 1 ? 2 : 3) enco
         const uint32_t nsub = enc_subs_per_tile<Sym>(max_len, a.nsub_cap);
         const uint64_t TILE = (uint64_t)enc_sub_syms<Sym>() * nsub;
         total = (uint32_t)((a.one.n + TILE - 1) / TILE);
-        r = enc_clamp_r<Sym>(a.reduce_log2 >= 0 ? a.reduce_log2 : enc_rule_r(hdr->total_bits, hdr->nsymbols));
+        r = enc_clamp_r<Sym>(a.reduce_log2 >= 0 ? a.reduce_log2
+                                                : enc_rule_r(hdr->total_bits, hdr->nsymbols, (int)fmt_wlog(a.one.format)));
         e32 = max_len <= 23;
         nsub1 = nsub;
         max_len1 = max_len;
@@ -1019,19 +1087,25 @@ __global__ void __launch_bounds__(kEncCtaThreads, sizeof(Sym) == 1 ? 2 : 3) enco
         bool done = false;
         if constexpr (GTAB && !BATCH) {
             if (a.etab) {
-                merge_dispatch<Sym, uint32_t, 2, BATCH>(r, a, fields, tbase, stage, ring, const_cast<uint32_t *>(a.etab),
+                merge_dispatch<Sym, uint32_t, 2, BATCH, CALIGN>(r, a, fields, tbase, stage, ring, const_cast<uint32_t *>(a.etab),
                                                         total, nsub1, max_len1, S);
                 done = true;
             }
         }
         if (!done)
-            merge_dispatch<Sym, uint32_t, kTab, BATCH>(r, a, fields, tbase, stage, ring,
+            merge_dispatch<Sym, uint32_t, kTab, BATCH, CALIGN>(r, a, fields, tbase, stage, ring,
                                                        GTAB ? nullptr : reinterpret_cast<uint32_t *>(tab), total, nsub1,
                                                        max_len1, S);
     } else {
-        merge_dispatch<Sym, uint64_t, kTab, BATCH>(r, a, fields, tbase, stage, ring, GTAB ? nullptr : tab, total, nsub1,
+        merge_dispatch<Sym, uint64_t, kTab, BATCH, CALIGN>(r, a, fields, tbase, stage, ring, GTAB ? nullptr : tab, total, nsub1,
                                                    max_len1, S);
     }
 }
+
+// The single-field kernel with the chunk-aligned layout's padding in the
+// tile scan (instantiated in encode_aligned.cu, apart from the dense kernels).
+using EncKernelFn = void (*)(EncArgs);
+template <typename Sym>
+EncKernelFn encode_kernel_aligned(bool gtab);
 
 }  // namespace huff

@@ -75,8 +75,13 @@ struct EncField {
     uint32_t nsub;           // sub-tiles per tile
     uint32_t ntiles;
     uint32_t tile_base;      // global id of the field's first tile
-    uint32_t pad;
+    uint32_t format;         // stream format (fmt_* below); 0 = dense 32-bit words
 };
+
+// EncField::format: bits 0-1 code the unit width W (0: 32, 1: 16, 2: 8 bits),
+// bit 8 the chunk-aligned layout (every chunk starts at a unit boundary).
+__host__ __device__ inline uint32_t fmt_wlog(uint32_t f) { return 5u - (f & 3u); }
+__host__ __device__ inline bool fmt_chunk_aligned(uint32_t f) { return ((f >> 8) & 1u) != 0; }
 
 // Launch-wide values of a batched encode, written by the planner on the device.
 struct EncBatchConf {
@@ -86,17 +91,21 @@ struct EncBatchConf {
     uint32_t pad;
 };
 
+// Checks the format fields of p (word_bits, layout, with chunk_log2 and merge)
+// for dtype and returns the EncField::format code in *fmt.
+huff_status encode_format_of(const huff_params &p, huff_dtype dtype, uint32_t *fmt);
+// cap counts units of the format's W bits.
 huff_status encode_launch(const void *d_sym, uint64_t n, huff_dtype dtype, const void *d_codebook, uint32_t nbins,
-                          int chunk_log2, int reduce_log2, uint32_t *d_out, uint64_t cap, uint64_t *d_offs,
-                          uint64_t *d_total, uint8_t *scratch, uint32_t *status, cudaStream_t st);
+                          int chunk_log2, int reduce_log2, uint32_t format, uint32_t *d_out, uint64_t cap,
+                          uint64_t *d_offs, uint64_t *d_total, uint8_t *scratch, uint32_t *status, cudaStream_t st);
 // The same with two failure-detection knobs: id_offset is added to every tile
 // id the encoder takes (1 leaves tile 0 unencoded, so the look-back of tile 1
 // can only give up), and spin_limit bounds the look-back's polls (0: the
 // default limit).
 huff_status encode_launch_ex(const void *d_sym, uint64_t n, huff_dtype dtype, const void *d_codebook, uint32_t nbins,
-                             int chunk_log2, int reduce_log2, uint32_t *d_out, uint64_t cap, uint64_t *d_offs,
-                             uint64_t *d_total, uint8_t *scratch, uint32_t *status, cudaStream_t st, uint32_t id_offset,
-                             uint32_t spin_limit);
+                             int chunk_log2, int reduce_log2, uint32_t format, uint32_t *d_out, uint64_t cap,
+                             uint64_t *d_offs, uint64_t *d_total, uint8_t *scratch, uint32_t *status, cudaStream_t st,
+                             uint32_t id_offset, uint32_t spin_limit);
 size_t encode_scratch_bytes(uint64_t n, uint32_t nbins);
 int encode_run_log2(huff_dtype dtype);
 // Symbols per sub-tile (the smallest tile) of a dtype.
@@ -119,8 +128,10 @@ huff_status encode_shuffle_launch(const void *d_sym, uint64_t n, huff_dtype dtyp
 
 // ---------------------------------------------------------------- decode
 
-huff_status decode_launch(const uint32_t *d_in, uint64_t total_bits, const uint64_t *d_offs, int chunk_log2,
-                          uint64_t n, huff_dtype dtype, const void *d_codebook, uint32_t nbins, void *d_out,
-                          uint32_t *status, cudaStream_t st);
+// format as EncField::format: d_in holds units of W bits; chunk-aligned
+// offsets count units.
+huff_status decode_launch(const void *d_in, uint64_t total_bits, const uint64_t *d_offs, int chunk_log2,
+                          uint32_t format, uint64_t n, huff_dtype dtype, const void *d_codebook, uint32_t nbins,
+                          void *d_out, uint32_t *status, cudaStream_t st);
 
 }  // namespace huff

@@ -83,6 +83,8 @@ extern "C" huff_status huff_encode_noalloc(const void *d_sym, uint64_t n, huff_d
     // the fixed array is sized for the fused encoder only: the paper-layout
     // merge (HUFF_MERGE_SHUFFLE) needs chunk slots it does not have
     if (prm.merge != HUFF_MERGE_AUTO && prm.merge != HUFF_MERGE_SCAN) return HUFF_ERR_INVALID_ARG;
+    uint32_t fmt = 0;
+    if (encode_format_of(prm, dtype, &fmt) != HUFF_OK) return HUFF_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     huff_status err = HUFF_OK;
     uint8_t *scratch = noalloc_scratch(st, &err);
@@ -95,6 +97,6 @@ extern "C" huff_status huff_encode_noalloc(const void *d_sym, uint64_t n, huff_d
     }
     // the encoder clears the part of the scratch it uses before its launch
     if (encode_scratch_bytes(n, nbins) > kNoAllocScratchBytes) return HUFF_ERR_INVALID_ARG;
-    return encode_launch(d_sym, n, dtype, d_codebook, nbins, prm.chunk_log2, prm.reduce_log2, d_out,
+    return encode_launch(d_sym, n, dtype, d_codebook, nbins, prm.chunk_log2, prm.reduce_log2, fmt, d_out,
                          out_capacity_words, d_chunk_bit_offset, d_total_bits, scratch, d_status, st);
 }

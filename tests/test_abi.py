@@ -70,7 +70,7 @@ def test_workspace_grows_with_n(lib):
 def test_default_params(lib):
     import paper_2010_10039_gb300 as huff
     p = huff.huff_default_params()
-    assert (p.chunk_log2, p.reduce_log2, p.block_threads, p.merge) == (10, -1, 0, 0)
+    assert (p.chunk_log2, p.reduce_log2, p.block_threads, p.merge, p.word_bits, p.layout) == (10, -1, 0, 0, 32, 0)
 
 
 def test_misaligned_typed_pointers_are_rejected_on_the_host(lib):
