@@ -60,7 +60,10 @@ typedef enum {
 } huff_status;
 
 #define HUFF_MAX_LEN 64            /* codeword lengths are 1..HUFF_MAX_LEN               */
-#define HUFF_MAX_BINS 65536        /* alphabet sizes are 1..HUFF_MAX_BINS                */
+#define HUFF_MAX_BINS 1048576      /* alphabet sizes are 1..HUFF_MAX_BINS (2^20; above 65,536
+                                      for HUFF_U32 symbols only)                          */
+#define HUFF_MAX_BINS_BATCH 65536  /* alphabet limit of the batched, served and
+                                      allocation-free forms                               */
 #define HUFF_CW_LEN_SHIFT 58       /* cw = code | (len << 58)                             */
 
 /*
@@ -167,7 +170,7 @@ huff_status huff_workspace_init(void *d_ws, void *stream);
  * Histogram (Sec. IV-A): d_hist[k] = number of i < n with d_sym[i] == k.
  *   d_sym   n symbols of `dtype`, aligned to the element size (16-byte aligned is fastest)
  *   n       < 2^32; 0 gives an all-zero histogram
- *   nbins   1..65536 (<= 256 for HUFF_U8)
+ *   nbins   1..HUFF_MAX_BINS (<= 256 for HUFF_U8, <= 65536 for HUFF_U16)
  *   d_hist  nbins uint32, overwritten
  * A symbol >= nbins records HUFF_ERR_SYMBOL_RANGE and is not counted.
  */
@@ -309,7 +312,7 @@ typedef struct {
     const void *d_sym;              /* n symbols of dtype, element aligned                            */
     uint64_t n;                     /* < 2^32                                                         */
     huff_dtype dtype;
-    uint32_t nbins;                 /* 1..65536 (<= 256 for HUFF_U8)                                  */
+    uint32_t nbins;                 /* 1..HUFF_MAX_BINS_BATCH (<= 256 for HUFF_U8)                    */
     int32_t chunk_log2;             /* M, 4..30; -1 = chosen by the plan from {10, 12, 14}: size the
                                        offsets for M = 10                                            */
     uint32_t reserved;

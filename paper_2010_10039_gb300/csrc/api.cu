@@ -62,6 +62,7 @@ static bool dtype_ok(huff_dtype d) { return d == HUFF_U8 || d == HUFF_U16 || d =
 static bool nbins_ok(huff_dtype d, uint32_t nbins) {
     if (nbins < 1 || nbins > HUFF_MAX_BINS) return false;
     if (d == HUFF_U8 && nbins > 256) return false;
+    if (d == HUFF_U16 && nbins > 65536) return false;
     return true;
 }
 

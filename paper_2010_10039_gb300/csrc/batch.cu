@@ -70,7 +70,7 @@ namespace {
 bool field_ok(const huff_field &f) {
     const huff_dtype d = f.dtype;
     if (d != HUFF_U8 && d != HUFF_U16 && d != HUFF_U32) return false;
-    if (f.nbins < 1 || f.nbins > HUFF_MAX_BINS || (d == HUFF_U8 && f.nbins > 256)) return false;
+    if (f.nbins < 1 || f.nbins > HUFF_MAX_BINS_BATCH || (d == HUFF_U8 && f.nbins > 256)) return false;
     if (f.n >= (1ull << 32)) return false;
     if (!f.d_chunk_bit_offset || !f.d_total_bits) return false;
     if (f.n && (!f.d_sym || !f.d_out)) return false;

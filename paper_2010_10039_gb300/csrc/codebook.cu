@@ -43,6 +43,12 @@ constexpr uint32_t kCbRevDepth = 16384;    // above this many used symbols, dept
 constexpr uint32_t kRadixDigits = 256;     // 8-bit digits of the large-alphabet sort
 constexpr uint32_t kRhStride = 34;         // u16 per digit row of the counting table: 17 words, odd, so
                                            // one warp's distinct digits fall in distinct banks
+constexpr uint32_t kSmallAlphabet = 65536; // above this the sort keys carry 32-bit ids and the
+                                           // counting table 32-bit slots (BIG instantiations)
+
+// Counting-table slot type and row stride (odd in words) of the two forms.
+template <bool BIG> struct RhOf { using T = uint16_t; static constexpr uint32_t kStride = kRhStride; };
+template <> struct RhOf<true> { using T = uint32_t; static constexpr uint32_t kStride = 33; };
 
 struct CbArrays {
     uint64_t *keys;     // 2P      sort keys (count << 16 | id); the two halves are the
@@ -127,8 +133,9 @@ __device__ __forceinline__ uint64_t bitonic_sort_regs(uint64_t x, uint32_t P, ui
 // digit-major, then element order.  Warp w owns a contiguous segment of the
 // elements; its per-digit counts rh[digit][w], scanned in digit-major order,
 // give its first slot for each digit, and the lanes of one step rank among
-// themselves by a warp match.  Counts and slots stay below 65,536 (len is at
-// most HUFF_MAX_BINS), so the table is u16, its rows padded to kRhStride.
+// themselves by a warp match.  Up to 65,536 elements the counts and slots stay
+// below 65,536 and the table is u16, its rows padded to kRhStride; larger
+// alphabets (BIG) take u32 slots.
 // elem(i) returns an element, four at a time so that their loads overlap.
 
 struct CpElem {
@@ -150,14 +157,14 @@ __device__ __forceinline__ void cp_segment(uint32_t len, uint32_t &begin, uint32
 // holding rh[digit][warp]; a count stays below 65,536, so nothing carries
 // into the neighbour), which beats the warp match when a step holds many
 // distinct digits; the match wins when they repeat.
-template <bool ATOMIC, typename Elem>
-__device__ void cpass_count(uint32_t len, Elem elem, uint16_t (*rh)[kRhStride], uint32_t *wsum, uint32_t *totals,
+template <bool ATOMIC, typename Elem, typename Slot, uint32_t STRIDE>
+__device__ void cpass_count(uint32_t len, Elem elem, Slot (*rh)[STRIDE], uint32_t *wsum, uint32_t *totals,
                             uint32_t ntotals) {
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t lt = (1u << lane) - 1;
     uint32_t begin, end;
     cp_segment(len, begin, end);
-    for (uint32_t i = tid; i < kRadixDigits * kRhStride; i += kCbThreads) (&rh[0][0])[i] = 0;
+    for (uint32_t i = tid; i < kRadixDigits * STRIDE; i += kCbThreads) (&rh[0][0])[i] = 0;
     __syncthreads();
     for (uint32_t b = begin; b < end; b += 128) {
         CpElem e[4];
@@ -169,11 +176,15 @@ __device__ void cpass_count(uint32_t len, Elem elem, uint16_t (*rh)[kRhStride], 
 #pragma unroll
         for (int q = 0; q < 4; q++) {
             if (ATOMIC) {
-                if (e[q].valid)
-                    atomicAdd(reinterpret_cast<uint32_t *>(&rh[e[q].digit][warp & ~1u]), 1u << (16 * (warp & 1)));
+                if (e[q].valid) {
+                    if (sizeof(Slot) == 2)
+                        atomicAdd(reinterpret_cast<uint32_t *>(&rh[e[q].digit][warp & ~1u]), 1u << (16 * (warp & 1)));
+                    else
+                        atomicAdd(reinterpret_cast<uint32_t *>(&rh[e[q].digit][warp]), 1u);
+                }
             } else {
                 const uint32_t peers = __match_any_sync(0xFFFFFFFFu, e[q].valid ? e[q].digit : 0x10000u);
-                if (e[q].valid && __popc(peers & lt) == 0) rh[e[q].digit][warp] += (uint16_t)__popc(peers);
+                if (e[q].valid && __popc(peers & lt) == 0) rh[e[q].digit][warp] += (Slot)__popc(peers);
             }
         }
     }
@@ -185,7 +196,7 @@ __device__ void cpass_count(uint32_t len, Elem elem, uint16_t (*rh)[kRhStride], 
     }
     // exclusive scan in digit-major order: eight entries per thread (digit
     // tid / 4, warps 8 * (tid % 4) ..)
-    uint16_t *row = &rh[tid >> 2][8 * (tid & 3)];
+    Slot *row = &rh[tid >> 2][8 * (tid & 3)];
     uint32_t v[8], sum = 0;
 #pragma unroll
     for (int q = 0; q < 8; q++) { v[q] = row[q]; sum += v[q]; }
@@ -201,15 +212,15 @@ __device__ void cpass_count(uint32_t len, Elem elem, uint16_t (*rh)[kRhStride], 
     for (uint32_t w = 0; w < warp; w++) wbase += wsum[w];
     uint32_t run = wbase + inc - sum;
 #pragma unroll
-    for (int q = 0; q < 8; q++) { row[q] = (uint16_t)run; run += v[q]; }
+    for (int q = 0; q < 8; q++) { row[q] = (Slot)run; run += v[q]; }
     __syncthreads();
 }
 
 // Hands every element with a digit to place(slot, payload) and every other
 // one to skip(payload), in the same element order as cpass_count.  Ends with
 // a barrier.
-template <typename Elem, typename Place, typename Skip>
-__device__ void cpass_scatter(uint32_t len, Elem elem, Place place, Skip skip, uint16_t (*rh)[kRhStride]) {
+template <typename Elem, typename Place, typename Skip, typename Slot, uint32_t STRIDE>
+__device__ void cpass_scatter(uint32_t len, Elem elem, Place place, Skip skip, Slot (*rh)[STRIDE]) {
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1;
     uint32_t begin, end;
@@ -229,7 +240,7 @@ __device__ void cpass_scatter(uint32_t len, Elem elem, Place place, Skip skip, u
             const uint32_t rank = __popc(peers & lt);
             const uint32_t slot = e[q].valid ? rh[e[q].digit][warp] : 0u;
             __syncwarp();
-            if (e[q].valid && rank == 0) rh[e[q].digit][warp] = (uint16_t)(slot + __popc(peers));
+            if (e[q].valid && rank == 0) rh[e[q].digit][warp] = (Slot)(slot + __popc(peers));
             __syncwarp();
             if (e[q].valid) place(slot + rank, e[q].payload);
             else if (in[q]) skip(e[q].payload);
@@ -239,24 +250,26 @@ __device__ void cpass_scatter(uint32_t len, Elem elem, Place place, Skip skip, u
 }
 
 // Stable LSD radix sort, by count, of the used bins of hist[nbins] into
-// buf[0, m) as keys count << 16 | id.  Bins enter in id order, so equal counts
+// buf[0, m) as keys count << IDB | id (IDB = 16, or 32 above 65,536 bins).  Bins enter in id order, so equal counts
 // stay in id order and the result is the (count, id) order.  8-bit digits,
 // as many passes as maxcount has digits; pass 0 reads the histogram and drops
 // unused bins, and the passes alternate between buf[0, P) and buf[P, 2P) so
 // that the last one lands in buf[0, P).
+template <bool BIG>
 __device__ void radix_sort_keys(const uint32_t *hist, uint32_t nbins, uint32_t m, uint32_t maxcount, uint64_t *buf,
-                                uint32_t P, uint16_t (*rh)[kRhStride], uint32_t *wsum) {
+                                uint32_t P, typename RhOf<BIG>::T (*rh)[RhOf<BIG>::kStride], uint32_t *wsum) {
+    constexpr uint32_t IDB = BIG ? 32 : 16;
     const uint32_t bits = 32 - __clz(maxcount);
     const uint32_t npass = bits > 8 ? (bits + 7) / 8 : 1;
     for (uint32_t pass = 0; pass < npass; pass++) {
-        const uint32_t shift = 16 + 8 * pass;
+        const uint32_t shift = IDB + 8 * pass;
         const uint64_t *src = buf + ((npass - pass) & 1) * P;
         uint64_t *dst = buf + ((npass - 1 - pass) & 1) * P;
         auto elem = [&](uint32_t i) -> CpElem {
             uint64_t key;
             if (pass == 0) {
                 const uint32_t c = hist[i];
-                key = ((uint64_t)c << 16) | i;
+                key = ((uint64_t)c << IDB) | i;
                 if (c == 0) return CpElem{false, 0u, key};
             } else {
                 key = src[i];
@@ -323,12 +336,16 @@ __device__ uint32_t warp_upper_bound(const uint32_t *w, uint32_t lo, uint32_t hi
 }
 
 // Builds the codebook of one histogram with the whole CTA; `arrays` holds the
-// construction's arrays (shared memory for small alphabets).
+// construction's arrays (shared memory for small alphabets).  BIG: alphabets
+// above 65,536 bins (32-bit ids in the sort keys, 32-bit counting slots).
+template <bool BIG>
 __device__ __forceinline__ void codebook_body(const CbArgs &g, uint8_t *arrays) {
+    constexpr uint32_t IDB = BIG ? 32 : 16;
+    constexpr uint64_t kIdMask = (1ull << IDB) - 1;
     __shared__ uint64_t s_sum, s_tbits;
     __shared__ uint32_t s_m, s_maxlen, s_bad, s_maxc, s_rounds;
     __shared__ uint32_t s_wsum[kCbThreads / 32];
-    __shared__ uint16_t s_rh[kRadixDigits][kRhStride];
+    __shared__ typename RhOf<BIG>::T s_rh[kRadixDigits][RhOf<BIG>::kStride];
     __shared__ uint32_t s_count[HUFF_MAX_LEN + 1];
     __shared__ uint32_t s_base[HUFF_MAX_LEN + 1];
     __shared__ uint64_t s_first[HUFF_MAX_LEN + 1];
@@ -360,7 +377,7 @@ __device__ __forceinline__ void codebook_body(const CbArgs &g, uint8_t *arrays) 
         maxc = c > maxc ? c : maxc;
         A.lenS[i] = 0;
         mycount = c;
-        if (small && c) mykey = ((uint64_t)c << 16) | i;
+        if (small && c) mykey = ((uint64_t)c << IDB) | i;
     }
     for (int o = 16; o; o >>= 1) {
         part += __shfl_xor_sync(0xFFFFFFFFu, part, o);
@@ -401,10 +418,10 @@ __device__ __forceinline__ void codebook_body(const CbArgs &g, uint8_t *arrays) 
             __syncthreads();
             if (tid < Ps) A.keys[tid] = mykey;
         } else {
-            radix_sort_keys(g.hist, nbins, m, s_maxc, A.keys, P, s_rh, s_wsum);
+            radix_sort_keys<BIG>(g.hist, nbins, m, s_maxc, A.keys, P, s_rh, s_wsum);
         }
         __syncthreads();
-        for (uint32_t i = tid; i < m; i += kCbThreads) A.wL[i] = (uint32_t)(A.keys[i] >> 16);
+        for (uint32_t i = tid; i < m; i += kCbThreads) A.wL[i] = (uint32_t)(A.keys[i] >> IDB);
         __syncthreads();
 
         // ---- GenerateCL rounds.  c leaves and the joined nodes before ih have
@@ -478,7 +495,7 @@ __device__ __forceinline__ void codebook_body(const CbArgs &g, uint8_t *arrays) 
                 uint32_t d = 0, x = v;
                 while (x != root && d <= HUFF_MAX_LEN) { x = A.parent[x]; d++; }
                 if (d > HUFF_MAX_LEN) { bad = 1; d = HUFF_MAX_LEN; }
-                A.lenS[(uint32_t)(A.keys[v] & 0xFFFF)] = (uint8_t)d;
+                A.lenS[(uint32_t)(A.keys[v] & kIdMask)] = (uint8_t)d;
             }
         } else {
             const uint32_t nI = m - 1, rounds = s_rounds;
@@ -493,7 +510,7 @@ __device__ __forceinline__ void codebook_body(const CbArgs &g, uint8_t *arrays) 
             for (uint32_t v = tid; v < m; v += kCbThreads) {
                 uint32_t d = A.depthI[A.parent[v] - m] + 1;
                 if (d > HUFF_MAX_LEN) { bad = 1; d = HUFF_MAX_LEN; }
-                A.lenS[(uint32_t)(A.keys[v] & 0xFFFF)] = (uint8_t)d;
+                A.lenS[(uint32_t)(A.keys[v] & kIdMask)] = (uint8_t)d;
             }
         }
         if (bad) s_bad = 1;
@@ -625,7 +642,12 @@ __device__ __forceinline__ void codebook_body(const CbArgs &g, uint8_t *arrays) 
 
 __global__ void __launch_bounds__(kCbThreads, 1) codebook_kernel(CbArgs g) {
     extern __shared__ __align__(16) uint8_t smem[];
-    codebook_body(g, g.nbins <= kCbSmemBins ? smem : g.scratch);
+    codebook_body<false>(g, g.nbins <= kCbSmemBins ? smem : g.scratch);
+}
+
+// Alphabets above 65,536 bins (arrays in the global scratch).
+__global__ void __launch_bounds__(kCbThreads, 1) codebook_big_kernel(CbArgs g) {
+    codebook_body<true>(g, g.scratch);
 }
 
 // Codebooks of a batch: CTA b builds those of fields b, b + grid, ...;
@@ -635,7 +657,7 @@ __global__ void __launch_bounds__(kCbThreads, 1) codebook_batch_kernel(const CbA
     extern __shared__ __align__(16) uint8_t smem[];
     for (uint32_t f = blockIdx.x; f < nfields; f += gridDim.x) {
         const CbArgs g = gs[f];
-        codebook_body(g, g.nbins <= kCbSmemBins ? smem : scratch + blockIdx.x * scratch_stride);
+        codebook_body<false>(g, g.nbins <= kCbSmemBins ? smem : scratch + blockIdx.x * scratch_stride);
         __syncthreads();     // the next field reuses the shared state
     }
 }
@@ -675,6 +697,11 @@ huff_status codebook_launch(const uint32_t *d_hist, uint32_t nbins, void *d_code
     a.book = static_cast<uint8_t *>(d_codebook);
     a.scratch = scratch;
     a.status = status;
+    if (nbins > kSmallAlphabet) {
+        codebook_big_kernel<<<1, kCbThreads, 0, st>>>(a);
+        note_launch();
+        return cudaGetLastError() == cudaSuccess ? HUFF_OK : HUFF_ERR_CUDA;
+    }
     size_t smem = nbins <= kCbSmemBins ? cb_array_bytes(nbins) : 0;
     if (!allow_dynamic_smem((const void *)codebook_kernel, smem))
         return HUFF_ERR_CUDA;

@@ -4,9 +4,9 @@
 // encoder let every chunk be decoded independently: one thread per chunk.
 //
 // GB300 form.  Every CTA first tabulates that rule in shared memory:
-//   level 1, over windows of L = min(max_len, 12) bits: symbol << 16 | length
+//   level 1, over windows of L = min(max_len, 12) bits: symbol << 10 | length
 //     for a code of at most L bits, kDecInvalid when no code starts there, and
-//     for a prefix of longer codes either kDecLong | subtable << 16 or 0;
+//     for a prefix of longer codes either kDecLong | subtable << 10 or 0;
 //   level 2, one subtable of 2^(max_len - L) entries per such prefix, indexed
 //     by the next max_len - L bits, when they fit (at most kL2Bits bits and
 //     kL2Entries entries in all).
@@ -27,8 +27,9 @@ namespace huff {
 constexpr int kDecThreads = 256;
 constexpr uint32_t kLutBits = 12;
 constexpr uint32_t kDecPairBins = 1024;     // two-code table entries for alphabets up to this size
-constexpr uint32_t kDecInvalid = 0x8000u;   // table entry: no codeword starts with this window
-constexpr uint32_t kDecLong = 0x4000u;      // level-1 entry: prefix of longer codes, subtable index in bits 16..31
+constexpr uint32_t kDecSymShift = 10;       // table entries: symbol (up to 22 bits) << kDecSymShift | length
+constexpr uint32_t kDecInvalid = 0x200u;    // table entry: no codeword starts with this window
+constexpr uint32_t kDecLong = 0x100u;       // level-1 entry: prefix of longer codes, subtable index from bit 10
 constexpr uint32_t kL2Bits = 8;             // longest level-2 index
 constexpr uint32_t kL2Entries = 4096;       // level-2 entries in all
 
@@ -144,9 +145,9 @@ __device__ __forceinline__ void decode_chunk(const DecArgs &a, const uint32_t *g
     // one code from a refilled buffer
     auto single = [&](uint32_t &s) {
         uint32_t e = dec_lut[hi >> shL];
-        if (e & kDecLong) e = dec_lut2[(e >> 16) * (m2 + 1) + ((hi >> sh2) & m2)];
+        if (e & kDecLong) e = dec_lut2[(e >> kDecSymShift) * (m2 + 1) + ((hi >> sh2) & m2)];
         uint32_t l = e & 0xFFu;
-        s = e >> 16;
+        s = e >> kDecSymShift;
         if (l == 0) {
             // no code (kDecInvalid), or longer than the tables: the search, on
             // the buffer when it holds max_len bits, else on a fresh window
@@ -280,7 +281,7 @@ __global__ void __launch_bounds__(kDecThreads) decode_kernel(DecArgs a) {
             if (v >= dec_first[l]) {
                 if (v - dec_first[l] < dec_count[l]) {
                     const uint32_t k = dec_entry[l] + (uint32_t)(v - dec_first[l]);
-                    e = (__ldg(sorted_syms + k) << 16) | l;
+                    e = (__ldg(sorted_syms + k) << kDecSymShift) | l;
                 } else {
                     e = kDecInvalid;
                 }
@@ -310,7 +311,7 @@ __global__ void __launch_bounds__(kDecThreads) decode_kernel(DecArgs a) {
         for (uint32_t x = x0; x < x0 + per && x < nwin; x++)
             if (dec_lut[x] == 0) {
                 dec_lpfx[base] = (uint16_t)x;
-                dec_lut[x] = kDecLong | (base++ << 16);
+                dec_lut[x] = kDecLong | (base++ << kDecSymShift);
             }
     }
     __syncthreads();
@@ -325,7 +326,7 @@ __global__ void __launch_bounds__(kDecThreads) decode_kernel(DecArgs a) {
                 if (v >= dec_first[l]) {
                     if (v - dec_first[l] < dec_count[l]) {
                         const uint32_t k = dec_entry[l] + (uint32_t)(v - dec_first[l]);
-                        e = (__ldg(sorted_syms + k) << 16) | l;
+                        e = (__ldg(sorted_syms + k) << kDecSymShift) | l;
                     }
                     break;
                 }
@@ -344,13 +345,13 @@ __global__ void __launch_bounds__(kDecThreads) decode_kernel(DecArgs a) {
             const uint32_t l1 = e1 & 0xFFu;
             uint32_t e = 0;
             if (l1 != 0) {
-                e = (e1 >> 16) | (l1 << 20);
+                e = (e1 >> kDecSymShift) | (l1 << 20);
                 // the rest of the window, shifted up; its low l1 bits are unknown,
                 // so a second code counts only if it lies within the known bits
                 const uint32_t x2 = (x << l1) & (nwin - 1);
                 const uint32_t f = dec_lut[x2];
                 const uint32_t l2 = f & 0xFFu;
-                if (l2 != 0 && l2 <= L - l1) e |= ((f >> 16) << 10) | (l2 << 24);
+                if (l2 != 0 && l2 <= L - l1) e |= ((f >> kDecSymShift) << 10) | (l2 << 24);
             }
             dec_pair[x] = e;
         }

@@ -51,6 +51,8 @@ struct SymVec<uint32_t> {
 };
 
 struct HistArgs {
+    uint32_t nwin;            // windows of 65,536 bins (alphabets above 65,536 bins); 1 otherwise
+    uint32_t pad;
     const uint8_t *base;      // first byte of the input
     uint64_t n;               // symbols
     uint64_t head;            // symbols before the first 16-byte aligned address
@@ -208,6 +210,82 @@ __global__ void __launch_bounds__(hist_threads(PACKED), PACKED ? 1 : 2) hist_ker
     if (bad || seen > mask) set_error(a.status, HUFF_ERR_SYMBOL_RANGE);
 }
 
+// ---------------------------------------------------------------- alphabets above 65,536 bins
+
+// The bins are split into windows of 65,536 packed counters (the most one
+// CTA's shared memory holds), and the grid into nwin groups of CTAs: group w
+// counts the symbols in [w * 65536, (w + 1) * 65536), reading all of the
+// input, so each CTA still owns every counter it increments (hot bins
+// contend only inside one CTA) and folds one window at the end.  The input
+// is read nwin times; the alternative of sending each symbol to the CTA that
+// owns its bin serialises the hot bins of skewed alphabets on one SM.
+// Counters, carries and epochs are those of the packed 65,536-bin kernel.
+template <typename Sym>
+__global__ void __launch_bounds__(kHistPackedThreads, 1) hist_window_kernel(HistArgs a) {
+    constexpr int T = kHistPackedThreads;
+    extern __shared__ __align__(16) uint32_t hsm[];
+    for (uint32_t i = threadIdx.x; i < kPackedWords; i += blockDim.x) hsm[i] = 0;
+    __syncthreads();
+    const uint32_t win = blockIdx.x % a.nwin, grp = blockIdx.x / a.nwin, ngrp = gridDim.x / a.nwin;
+    const uint32_t lo = win << 16;
+    uint32_t seen = 0, bad = 0;
+    auto count = [&](uint32_t s) {
+        seen |= s;
+        const uint32_t d = s - lo;
+        if (d < 65536u) {
+            const uint32_t sh = (d >> 15) << 4;
+            uint32_t *w = hsm + (d & (kPackedWords - 1));
+            const uint32_t old = atomicAdd(w, 1u << sh);
+            if (((old >> sh) & 0xFFFFu) == 0x7FFFu) {
+                atomicSub(w, 0x8000u << sh);
+                if (s < a.nbins) atomicAdd(a.hist + s, 0x8000u); else bad = 1;
+            }
+        }
+    };
+    const uint4 *vec = reinterpret_cast<const uint4 *>(a.base + a.head * sizeof(Sym));
+    constexpr uint64_t kRound = 2ull * T;
+    constexpr uint32_t kSymsPerRound = kRound * SymVec<Sym>::N;
+    constexpr uint32_t kRoundsPerEpoch = 32768u / kSymsPerRound;
+    static_assert(kRoundsPerEpoch >= 1, "a round must fit in an epoch");
+    const uint64_t nrounds = (a.nvec + kRound - 1) / kRound;
+    uint32_t since = 0;
+    for (uint64_t r = grp; r < nrounds; r += ngrp) {
+        const uint64_t i0 = r * kRound + threadIdx.x, i1 = i0 + T;
+        if (i1 < a.nvec) {
+            const uint4 v0 = vec[i0], v1 = vec[i1];
+#pragma unroll
+            for (int j = 0; j < SymVec<Sym>::N; j++) count(SymVec<Sym>::get(v0, j));
+#pragma unroll
+            for (int j = 0; j < SymVec<Sym>::N; j++) count(SymVec<Sym>::get(v1, j));
+        } else if (i0 < a.nvec) {
+            const uint4 v0 = vec[i0];
+#pragma unroll
+            for (int j = 0; j < SymVec<Sym>::N; j++) count(SymVec<Sym>::get(v0, j));
+        }
+        if (++since == kRoundsPerEpoch) {
+            __syncthreads();
+            since = 0;
+        }
+    }
+    __syncthreads();
+    const uint64_t tail0 = a.head + a.nvec * SymVec<Sym>::N;
+    const Sym *sp = reinterpret_cast<const Sym *>(a.base);
+    const uint64_t nrest = a.head + (a.n - tail0);
+    for (uint64_t i = grp * (uint64_t)blockDim.x + threadIdx.x; i < nrest; i += (uint64_t)ngrp * blockDim.x)
+        count(sp[i < a.head ? i : tail0 + (i - a.head)]);
+    __syncthreads();
+    for (uint32_t w = threadIdx.x; w < kPackedWords; w += blockDim.x) {
+        const uint32_t v = hsm[w];
+        if (v & 0xFFFFu) {
+            if (lo + w < a.nbins) atomicAdd(a.hist + lo + w, v & 0xFFFFu); else bad = 1;
+        }
+        if (v >> 16) {
+            if (lo + w + kPackedWords < a.nbins) atomicAdd(a.hist + lo + w + kPackedWords, v >> 16); else bad = 1;
+        }
+    }
+    if (bad || seen > a.mask) set_error(a.status, HUFF_ERR_SYMBOL_RANGE);
+}
+
 // ---------------------------------------------------------------- batched histogram
 
 // Every CTA counts whole tiles (CTA-strided over the tile list) into its
@@ -271,10 +349,30 @@ static huff_status launch_hist(const void *d_sym, uint64_t n, uint32_t nbins, ui
     a.nbins = nbins;
     a.hist = d_hist;
     a.status = status;
-    const bool packed = nbins > 16384;
+    a.nwin = 1;
+    a.pad = 0;
     uint32_t slots = 1;
     while (slots < nbins) slots <<= 1;
     a.mask = slots - 1;
+    if (nbins > 65536) {
+        if (sizeof(Sym) != 4) return HUFF_ERR_INVALID_ARG;
+        a.nwin = (nbins + 65535) / 65536;
+        const size_t smem = kPackedWords * 4;
+        if (!allow_dynamic_smem((const void *)hist_window_kernel<Sym>, smem)) return HUFF_ERR_CUDA;
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hist_window_kernel<Sym>, kHistPackedThreads, smem);
+        if (occ < 1) occ = 1;
+        // every window gets the same number of CTAs, at least one
+        uint64_t per = (uint64_t)sm_count() * occ / a.nwin;
+        const uint64_t rounds = (a.nvec + 2ull * kHistPackedThreads - 1) / (2ull * kHistPackedThreads);
+        if (per > rounds) per = rounds;
+        if (per < 1) per = 1;
+        if (cudaMemsetAsync(d_hist, 0, nbins * sizeof(uint32_t), st) != cudaSuccess) return HUFF_ERR_CUDA;
+        hist_window_kernel<Sym><<<(unsigned)(per * a.nwin), kHistPackedThreads, smem, st>>>(a);
+        note_launch();
+        return cudaGetLastError() == cudaSuccess ? HUFF_OK : HUFF_ERR_CUDA;
+    }
+    const bool packed = nbins > 16384;
     size_t smem;
     if (packed) {
         a.nrep = 1;

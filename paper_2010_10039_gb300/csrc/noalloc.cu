@@ -17,7 +17,7 @@ namespace huff {
 // alphabet (256 KiB).
 constexpr uint64_t kNoAllocMaxSymbols = 1ull << 28;
 constexpr size_t kNoAllocScratchBytes =
-    ((64 + 16 * (kNoAllocMaxSymbols / 2048) + 255) & ~size_t(255)) + 4ull * HUFF_MAX_BINS;
+    ((64 + 16 * (kNoAllocMaxSymbols / 2048) + 255) & ~size_t(255)) + 4ull * HUFF_MAX_BINS_BATCH;
 
 // One copy per device that loads the library; it stays until the process exits.
 static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocScratchBytes];
@@ -73,7 +73,7 @@ extern "C" huff_status huff_encode_noalloc(const void *d_sym, uint64_t n, huff_d
     if (!d_status || !d_codebook || !d_chunk_bit_offset || !d_total_bits || (n && (!d_sym || !d_out)))
         return HUFF_ERR_INVALID_ARG;
     if (dtype != HUFF_U8 && dtype != HUFF_U16 && dtype != HUFF_U32) return HUFF_ERR_INVALID_ARG;
-    if (nbins < 1 || nbins > HUFF_MAX_BINS || (dtype == HUFF_U8 && nbins > 256)) return HUFF_ERR_INVALID_ARG;
+    if (nbins < 1 || nbins > HUFF_MAX_BINS_BATCH || (dtype == HUFF_U8 && nbins > 256)) return HUFF_ERR_INVALID_ARG;
     if (((uintptr_t)d_codebook & 15) != 0) return HUFF_ERR_INVALID_ARG;
     if (((uintptr_t)d_sym % (uintptr_t)dtype) != 0 || ((uintptr_t)d_out & 3) != 0 ||
         ((uintptr_t)d_chunk_bit_offset & 7) != 0 || ((uintptr_t)d_total_bits & 7) != 0 || ((uintptr_t)d_status & 3) != 0)

@@ -362,7 +362,7 @@ bool request_ok(const huff_server *s, const huff_request *r) {
     if (!r) return false;
     const huff_dtype d = r->dtype;
     if (d != HUFF_U8 && d != HUFF_U16 && d != HUFF_U32) return false;
-    if (r->nbins < 1 || r->nbins > HUFF_MAX_BINS || (d == HUFF_U8 && r->nbins > 256)) return false;
+    if (r->nbins < 1 || r->nbins > HUFF_MAX_BINS_BATCH || (d == HUFF_U8 && r->nbins > 256)) return false;
     if (r->n < 1 || r->n > s->cfg.max_batch_symbols || r->n >= (1ull << 32) || !r->d_sym) return false;
     if (((uintptr_t)r->d_sym % (uintptr_t)d) != 0) return false;
     return true;
@@ -429,7 +429,7 @@ huff_status huff_serve_create(const huff_serve_cfg *cfg, huff_server **out) {
     // stream contexts: records, histograms, descriptors and scratch for one batch each
     const uint64_t max_tiles = c.max_batch_symbols / 32768 + c.max_batch + 1;
     const uint64_t enc_tiles = c.max_batch_symbols / 2048 + c.max_batch + 1;
-    const size_t cbscr_stride = align256(codebook_array_bytes(HUFF_MAX_BINS));
+    const size_t cbscr_stride = align256(codebook_array_bytes(HUFF_MAX_BINS_BATCH));
     s->ctxs.resize(c.nstreams);
     for (Ctx &x : s->ctxs) {
         x.srv = s;
@@ -440,7 +440,7 @@ huff_status huff_serve_create(const huff_serve_cfg *cfg, huff_server **out) {
         const size_t o_tiles = take(sizeof(HistTile) * max_tiles), o_hf = take(sizeof(HistField) * c.max_batch),
                      o_cb = take(sizeof(CbArgs) * c.max_batch), o_ef = take(sizeof(EncField) * c.max_batch),
                      o_conf = take(sizeof(EncBatchConf) * kMaxGroupsPerBatch),
-                     o_hist = take(4ull * HUFF_MAX_BINS * c.max_batch), o_status = take(4ull * c.max_batch),
+                     o_hist = take(4ull * HUFF_MAX_BINS_BATCH * c.max_batch), o_status = take(4ull * c.max_batch),
                      o_total = take(8ull * c.max_batch), o_escr = take(64 + 16 * enc_tiles),
                      o_cbscr = take(cbscr_stride * kCbScratchCtas);
         if (cudaMalloc(&x.dmem, off) != cudaSuccess) {
