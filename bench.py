@@ -36,8 +36,8 @@ WORKLOADS = {
     "served": (None, None, "Poisson arrivals at --rate req/s for --duration s; half u8 Zipf(1.2) over 256 ids, "
                            "half u16 Gaussian/Laplace(512, scale log-uniform in [1, 64]) over 1024 bins; n log-uniform "
                            "in [16384, 67108864]; payloads drawn on the device before arrival; seed 5"),
-    "large_alphabet": (1 << 26, 65536, "u32 Zipf(s=1.1) over 8,192 and 65,536 ids mapped through a seeded "
-                                       "permutation, 67,108,864 symbols per alphabet, seed 3"),
+    "large_alphabet": (1 << 26, 65536, "u32 Zipf(s=1.1) over 8,192, 65,536, 262,144 and 1,048,576 ids (--alphabets) "
+                                       "mapped through a seeded permutation, 67,108,864 symbols per alphabet, seed 3"),
     "batched_fields": (None, 1024, "512 u16 fields, n log-uniform in [65536, 16777216], Laplace(512, b ~ U[0.5, 16]) "
                                    "over 1024 bins, seed 4 (field j: stream j, size/scale from stream 10000+j)"),
 }
@@ -526,9 +526,10 @@ def run_ours(args, world, rank, local):
 # ----------------------------------------------------------------------------- large alphabets
 
 def run_large_alphabet(args, world, rank, local):
-    """The large-alphabet stress: 67,108,864 u32 Zipf(1.1) symbols over 8,192
-    and then 65,536 ids, each through histogram -> codebook -> encode, with
-    the codebook construction timed on its own.  A step is both alphabets."""
+    """The large-alphabet stress: 67,108,864 u32 Zipf(1.1) symbols over each
+    alphabet of --alphabets (8,192 to 1,048,576 ids, n-gram sized), each
+    through histogram -> codebook -> encode, with every stage timed on its
+    own.  A step is all alphabets."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -537,7 +538,7 @@ def run_large_alphabet(args, world, rank, local):
 
     torch.cuda.set_device(local)
     n = WORKLOADS["large_alphabet"][0]
-    alphabets = (8192, 65536)
+    alphabets = tuple(args.alphabets)
     params = {"chunk_log2": args.chunk_log2}
     fields = []
     for K in alphabets:
@@ -1216,6 +1217,8 @@ def main():
                     default=[2000.0, 4000.0, 8000.0, 16000.0, 32000.0, 64000.0, 128000.0],
                     help="served: open-loop rates of the sweep (req/s, comma separated)")
     ap.add_argument("--sweep-seconds", type=float, default=1.0, help="served: seconds of arrivals per sweep rate")
+    ap.add_argument("--alphabets", type=lambda v: [int(x) for x in v.split(",")],
+                    default=[8192, 65536, 262144, 1048576], help="large_alphabet: alphabet sizes")
     ap.add_argument("--no-sub-records", action="store_true",
                     help="hpc_field: leave out the batched and served sub-records")
     args = ap.parse_args()

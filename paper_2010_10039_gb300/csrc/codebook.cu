@@ -33,6 +33,8 @@
 // one length are consecutive in ascending symbol id (a warp-match rank inside
 // each 1024-id slice plus a per-length running base).  Entry and the
 // (length, id)-sorted symbol list form the reverse codebook.
+#include <cooperative_groups.h>
+
 #include "kernels.cuh"
 
 namespace huff {
@@ -640,6 +642,442 @@ __device__ __forceinline__ void codebook_body(const CbArgs &g, uint8_t *arrays) 
     }
 }
 
+// ---------------------------------------------------------------- cluster form
+//
+// Alphabets of more than kCcMinBins bins: one thread-block cluster of CL CTAs
+// (16 where the device allows it, else 8) builds the codebook.  The phases
+// whose work grows with the alphabet are split over the cluster's CTAs:
+//   sort      a stable LSD radix sort by count (8-bit digits); each CTA counts
+//             the digits of its share of the elements, reads every CTA's digit
+//             totals from distributed shared memory to find its first slot per
+//             digit, and scatters its share;
+//   depths    pointer jumping over the parent links (each node adds its
+//             parent's distance and takes its grandparent, seven times: depths
+//             up to 128), instead of one pass per round in reverse;
+//   codes     each CTA counts the lengths of its id range, reads every CTA's
+//             counts for First, Entry and its own base per length, and assigns
+//             the codes of its ids in id order.
+// A cluster barrier separates the phases.  The GenerateCL rounds stay on CTA 0:
+// a round's cost is the latency of its chain (selection, co-ranking search,
+// barrier), which more CTAs would lengthen by a cluster barrier per round.
+
+namespace cg = cooperative_groups;
+
+constexpr uint32_t kCcMinBins = 16385;     // alphabets from here on take the cluster form
+constexpr uint32_t kCcJumps = 7;           // pointer-jumping steps: depths up to 2^7
+
+// Scratch beyond CbArrays: parents and distances of the pointer jumping (two
+// buffers each, 2m entries) and the sorted leaves' symbol ids.
+__host__ __device__ inline size_t cc_extra_bytes(uint32_t nbins) {
+    return 4 * align16((size_t)nbins * 8) + align16((size_t)nbins * 4);
+}
+
+__device__ __forceinline__ void cc_split(uint32_t len, uint32_t parts, uint32_t i, uint32_t &lo, uint32_t &hi) {
+    lo = (uint32_t)((uint64_t)len * i / parts);
+    hi = (uint32_t)((uint64_t)len * (i + 1) / parts);
+}
+
+// Segment of warp `warp` inside the CTA's element range [e0, e1).
+__device__ __forceinline__ void cc_segment(uint32_t e0, uint32_t e1, uint32_t &begin, uint32_t &end) {
+    const uint32_t warp = threadIdx.x >> 5, len = e1 - e0;
+    const uint32_t seg = (((len + 31) / 32) + 31) & ~31u;
+    begin = e0 + (warp * seg < len ? warp * seg : len);
+    end = begin + seg < e1 ? begin + seg : e1;
+}
+
+struct CcShared {
+    uint32_t rh[kRadixDigits][33];      // per-warp digit counts, then slots
+    uint32_t tot[kRadixDigits];         // this CTA's digit totals (read by the cluster)
+    uint32_t wsum[kCbThreads / 32];
+    uint64_t sum;                       // this CTA's share of the histogram sum (read by the cluster)
+    uint32_t used, maxc, bad;           // (read by the cluster)
+    uint64_t g_sum;                     // cluster-wide values
+    uint32_t g_m, g_maxc, g_bad;
+    uint32_t lcnt[HUFF_MAX_LEN + 1];    // ids of each length in this CTA's range (read by the cluster)
+    uint32_t count[HUFF_MAX_LEN + 1], base[HUFF_MAX_LEN + 1], entry[HUFF_MAX_LEN + 1];
+    uint64_t first[HUFF_MAX_LEN + 1];
+    uint32_t wcnt[kCbThreads / 32][HUFF_MAX_LEN + 1];
+    uint64_t tb;                        // total bits (CTA 0 gathers the cluster's)
+    uint32_t maxlen;
+};
+
+// One stable counting pass of the cluster: elements [0, len), CTA R owning
+// [e0, e1); elem(i) gives the element (digit, payload); place(slot, payload)
+// receives it at its slot in digit-major, element order.  Ends with a cluster
+// barrier (every slot written).
+template <typename Elem, typename Place>
+__device__ void cc_pass(cg::cluster_group &cl, CcShared &S, uint32_t len, bool atomic_count, Elem elem, Place place) {
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t R = cl.block_rank(), CL = cl.num_blocks();
+    const uint32_t lt = (1u << lane) - 1;
+    uint32_t e0, e1, begin, end;
+    cc_split(len, CL, R, e0, e1);
+    cc_segment(e0, e1, begin, end);
+    for (uint32_t i = tid; i < kRadixDigits * 33; i += kCbThreads) (&S.rh[0][0])[i] = 0;
+    __syncthreads();
+    for (uint32_t b = begin; b < end; b += 128) {
+        CpElem e[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const uint32_t i = b + 32 * q + lane;
+            e[q] = i < end ? elem(i) : CpElem{false, 0u, 0ull};
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            if (atomic_count) {
+                if (e[q].valid) atomicAdd(&S.rh[e[q].digit][warp], 1u);
+            } else {
+                const uint32_t peers = __match_any_sync(0xFFFFFFFFu, e[q].valid ? e[q].digit : 0x10000u);
+                if (e[q].valid && __popc(peers & lt) == 0) S.rh[e[q].digit][warp] += __popc(peers);
+            }
+        }
+    }
+    __syncthreads();
+    if (tid < kRadixDigits) {
+        uint32_t t = 0;
+        for (uint32_t w = 0; w < 32; w++) t += S.rh[tid][w];
+        S.tot[tid] = t;
+    }
+    cl.sync();                                           // every CTA's totals are out
+    uint32_t pre = 0, all = 0;
+    if (tid < kRadixDigits) {
+        for (uint32_t r = 0; r < CL; r++) {
+            const uint32_t x = *cl.map_shared_rank(&S.tot[tid], r);
+            all += x;
+            if (r < R) pre += x;
+        }
+    }
+    // first slot of digit d in this CTA: elements of smaller digits anywhere,
+    // then this digit in the CTAs before this one
+    uint32_t inc = all;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (tid < kRadixDigits && lane == 31) S.wsum[warp] = inc;
+    __syncthreads();
+    if (tid < kRadixDigits) {
+        uint32_t wb = 0;
+        for (uint32_t w = 0; w < warp; w++) wb += S.wsum[w];
+        uint32_t run = wb + inc - all + pre;
+        for (uint32_t w = 0; w < 32; w++) {
+            const uint32_t c = S.rh[tid][w];
+            S.rh[tid][w] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    for (uint32_t b = begin; b < end; b += 128) {
+        CpElem e[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const uint32_t i = b + 32 * q + lane;
+            e[q] = i < end ? elem(i) : CpElem{false, 0u, 0ull};
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const uint32_t peers = __match_any_sync(0xFFFFFFFFu, e[q].valid ? e[q].digit : 0x10000u);
+            const uint32_t rank = __popc(peers & lt);
+            const uint32_t slot = e[q].valid ? S.rh[e[q].digit][warp] : 0u;
+            __syncwarp();
+            if (e[q].valid && rank == 0) S.rh[e[q].digit][warp] = slot + __popc(peers);
+            __syncwarp();
+            if (e[q].valid) place(slot + rank, e[q].payload);
+        }
+    }
+    cl.sync();                                           // every slot written; totals no longer read
+}
+
+__global__ void __launch_bounds__(kCbThreads, 1) codebook_cluster_kernel(CbArgs g) {
+    cg::cluster_group cl = cg::this_cluster();
+    __shared__ CcShared S;
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t R = cl.block_rank(), CL = cl.num_blocks();
+    const uint32_t nbins = g.nbins;
+    const uint32_t P = pow2_ceil(nbins);
+    CbArrays A = cb_carve(g.scratch, nbins);
+    uint8_t *xp = g.scratch + cb_array_bytes(nbins);
+    uint32_t *jp[2], *jd[2];
+    jp[0] = reinterpret_cast<uint32_t *>(xp); xp += align16((size_t)nbins * 8);
+    jp[1] = reinterpret_cast<uint32_t *>(xp); xp += align16((size_t)nbins * 8);
+    jd[0] = reinterpret_cast<uint32_t *>(xp); xp += align16((size_t)nbins * 8);
+    jd[1] = reinterpret_cast<uint32_t *>(xp); xp += align16((size_t)nbins * 8);
+    uint32_t *ids = reinterpret_cast<uint32_t *>(xp);
+    huff_codebook_header *hdr = reinterpret_cast<huff_codebook_header *>(g.book);
+    uint64_t *cw = reinterpret_cast<uint64_t *>(g.book + cb_cw_offset());
+    uint32_t *sorted_syms = reinterpret_cast<uint32_t *>(g.book + cb_sorted_offset(nbins));
+
+    // ---- this CTA's bins: sum, used, largest count; lengths cleared
+    uint32_t b0, b1;
+    cc_split(nbins, CL, R, b0, b1);
+    if (tid == 0) { S.sum = 0; S.used = 0; S.maxc = 0; S.bad = 0; S.tb = 0; }
+    if (tid <= HUFF_MAX_LEN) { S.lcnt[tid] = 0; S.first[tid] = 0; S.entry[tid] = 0; S.count[tid] = 0; }
+    __syncthreads();
+    {
+        uint64_t part = 0;
+        uint32_t used = 0, maxc = 0;
+        for (uint32_t i = b0 + tid; i < b1; i += kCbThreads) {
+            const uint32_t c = g.hist[i];
+            part += c;
+            used += c != 0;
+            maxc = c > maxc ? c : maxc;
+            A.lenS[i] = 0;
+        }
+        for (int o = 16; o; o >>= 1) {
+            part += __shfl_xor_sync(0xFFFFFFFFu, part, o);
+            used += __shfl_xor_sync(0xFFFFFFFFu, used, o);
+            maxc = max(maxc, __shfl_xor_sync(0xFFFFFFFFu, maxc, o));
+        }
+        if (lane == 0) {
+            atomicAdd((unsigned long long *)&S.sum, (unsigned long long)part);
+            atomicAdd(&S.used, used);
+            atomicMax(&S.maxc, maxc);
+        }
+    }
+    cl.sync();
+    if (warp == 0) {
+        uint64_t sum = 0;
+        uint32_t used = 0, maxc = 0;
+        if (lane < CL) {
+            sum = *cl.map_shared_rank(&S.sum, lane);
+            used = *cl.map_shared_rank(&S.used, lane);
+            maxc = *cl.map_shared_rank(&S.maxc, lane);
+        }
+        for (int o = 16; o; o >>= 1) {
+            sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
+            used += __shfl_xor_sync(0xFFFFFFFFu, used, o);
+            maxc = max(maxc, __shfl_xor_sync(0xFFFFFFFFu, maxc, o));
+        }
+        if (lane == 0) { S.g_sum = sum; S.g_m = used; S.g_maxc = maxc; }
+    }
+    __syncthreads();
+    const bool overflow = S.g_sum >= (1ull << 32);
+    const uint32_t m = overflow ? 0 : S.g_m;
+    if (overflow && R == 0 && tid == 0) set_error(g.status, HUFF_ERR_HIST_OVERFLOW);
+    uint32_t bad = 0;
+
+    if (m >= 2) {
+        // ---- sort: keys count << 32 | id, stable by count over ids in order
+        const uint32_t maxcount = S.g_maxc;
+        const uint32_t bits = 32 - __clz(maxcount);
+        const uint32_t npass = bits > 8 ? (bits + 7) / 8 : 1;
+        for (uint32_t pass = 0; pass < npass; pass++) {
+            const uint32_t shift = 32 + 8 * pass;
+            const uint64_t *src = A.keys + ((npass - pass) & 1) * P;
+            uint64_t *dst = A.keys + ((npass - 1 - pass) & 1) * P;
+            auto elem = [&](uint32_t i) -> CpElem {
+                uint64_t key;
+                if (pass == 0) {
+                    const uint32_t c = g.hist[i];
+                    key = ((uint64_t)c << 32) | i;
+                    if (c == 0) return CpElem{false, 0u, key};
+                } else {
+                    key = src[i];
+                }
+                return CpElem{true, (uint32_t)(key >> shift) & (kRadixDigits - 1), key};
+            };
+            cc_pass(cl, S, pass == 0 ? nbins : m, pass == 0 && maxcount >= 256, elem,
+                    [&](uint32_t slot, uint64_t key) { dst[slot] = key; });
+        }
+        {
+            uint32_t k0, k1;
+            cc_split(m, CL, R, k0, k1);
+            for (uint32_t i = k0 + tid; i < k1; i += kCbThreads) {
+                const uint64_t key = A.keys[i];
+                A.wL[i] = (uint32_t)(key >> 32);
+                ids[i] = (uint32_t)key;
+            }
+        }
+        cl.sync();
+
+        // ---- GenerateCL rounds on CTA 0 (the rule and its proof: codebook_body)
+        if (R == 0) {
+            const uint32_t rt = m <= 2048 ? 256u : (m <= 16384 ? 512u : (uint32_t)kCbThreads);
+            if (tid < rt) {
+                constexpr uint64_t kNone = 1ull << 33;
+                uint32_t c = 0, ih = 0, it = 0;
+                while ((m - c) + (it - ih) >= 2) {
+                    const uint64_t a0 = c < m ? A.wL[c] : kNone, a1 = c + 1 < m ? A.wL[c + 1] : kNone;
+                    const uint64_t bb0 = ih < it ? A.wI[ih] : kNone, bb1 = ih + 1 < it ? A.wI[ih + 1] : kNone;
+                    const uint64_t t = a0 <= bb0 ? a0 + (a1 <= bb0 ? a1 : bb0) : bb0 + (a0 <= bb1 ? a0 : bb1);
+                    uint32_t mL, mI;
+                    warp_upper_bound2(A.wL, c, m, A.wI, ih, it, (uint32_t)t, mL, mI);
+                    mL -= c;
+                    mI -= ih;
+                    if ((mL + mI) & 1) {
+                        const uint32_t lastI = mI ? A.wI[ih + mI - 1] : 0u, lastL = mL ? A.wL[c + mL - 1] : 0u;
+                        const bool dropI = mI > 0 && (mL == 0 || lastI >= lastL);
+                        if (dropI) mI--; else mL--;
+                    }
+                    const uint32_t pairs = (mL + mI) >> 1;
+                    const uint32_t *wa = A.wL + c, *wb = A.wI + ih;
+                    for (uint32_t j = tid; j < pairs; j += rt) {
+                        const uint32_t p = 2 * j;
+                        uint32_t lo = p > mI ? p - mI : 0, hi = p < mL ? p : mL;
+                        while (lo < hi) {
+                            const uint32_t mid = (lo + hi) >> 1;
+                            if (wa[mid] <= wb[p - 1 - mid]) lo = mid + 1; else hi = mid;
+                        }
+                        uint32_t ia = lo, ib = p - lo, wsum = 0;
+                        uint32_t node[2];
+#pragma unroll
+                        for (int q = 0; q < 2; q++) {
+                            const bool leaf = ia < mL && (ib >= mI || wa[ia] <= wb[ib]);
+                            if (leaf) { node[q] = c + ia; wsum += wa[ia]; ia++; }
+                            else { node[q] = m + ih + ib; wsum += wb[ib]; ib++; }
+                        }
+                        A.wI[it + j] = wsum;
+                        A.parent[node[0]] = m + it + j;
+                        A.parent[node[1]] = m + it + j;
+                    }
+                    c += mL;
+                    ih += mI;
+                    it += pairs;
+                    asm volatile("bar.sync 1, %0;" ::"r"(rt) : "memory");
+                }
+            }
+        }
+        cl.sync();
+
+        // ---- depths by pointer jumping over the 2m - 1 nodes (root 2m - 2)
+        const uint32_t nodes = 2 * m - 1, root = 2 * m - 2;
+        uint32_t v0, v1;
+        cc_split(nodes, CL, R, v0, v1);
+        for (uint32_t v = v0 + tid; v < v1; v += kCbThreads) {
+            jp[0][v] = v == root ? root : A.parent[v];
+            jd[0][v] = v == root ? 0u : 1u;
+        }
+        cl.sync();
+        uint32_t cur = 0;
+        for (uint32_t k = 0; k < kCcJumps; k++) {
+            const uint32_t *pc = jp[cur], *dc = jd[cur];
+            uint32_t *pn = jp[cur ^ 1], *dn = jd[cur ^ 1];
+            for (uint32_t v = v0 + tid; v < v1; v += kCbThreads) {
+                const uint32_t p = pc[v];
+                dn[v] = dc[v] + dc[p];
+                pn[v] = pc[p];
+            }
+            cur ^= 1;
+            cl.sync();
+        }
+        uint32_t l0, l1;
+        cc_split(m, CL, R, l0, l1);
+        for (uint32_t v = l0 + tid; v < l1; v += kCbThreads) {
+            uint32_t d = jd[cur][v];
+            if (jp[cur][v] != root || d > HUFF_MAX_LEN) { bad = 1; d = HUFF_MAX_LEN; }
+            A.lenS[ids[v]] = (uint8_t)d;
+        }
+    } else if (m == 1) {
+        for (uint32_t i = b0 + tid; i < b1; i += kCbThreads)
+            if (g.hist[i]) A.lenS[i] = 1;
+    }
+    if (bad) atomicOr(&S.bad, 1u);
+    cl.sync();                                           // lengths complete; every CTA's flag out
+    if (warp == 0) {
+        uint32_t any = lane < CL ? *cl.map_shared_rank(&S.bad, lane) : 0u;
+        any = __any_sync(0xFFFFFFFFu, any != 0);
+        if (lane == 0) S.g_bad = any;
+    }
+    __syncthreads();
+    const bool failed = overflow || S.g_bad;
+    if (S.g_bad && R == 0 && tid == 0) set_error(g.status, HUFF_ERR_HIST_OVERFLOW);
+
+    // ---- canonical codes: lengths of this CTA's ids, then the cluster's
+    // counts, First, Entry and this CTA's base per length
+    for (uint32_t i = b0 + tid; i < b1; i += kCbThreads) {
+        const uint32_t l = failed ? 0u : A.lenS[i];
+        if (l) atomicAdd(&S.lcnt[l], 1u);
+    }
+    cl.sync();
+    if (tid <= HUFF_MAX_LEN) {
+        uint32_t all = 0, pre = 0;
+        if (tid >= 1) {
+            for (uint32_t r = 0; r < CL; r++) {
+                const uint32_t x = *cl.map_shared_rank(&S.lcnt[tid], r);
+                all += x;
+                if (r < R) pre += x;
+            }
+        }
+        S.count[tid] = all;
+        S.base[tid] = pre;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t maxl = 0;
+        for (uint32_t l = 1; l <= HUFF_MAX_LEN; l++) if (S.count[l]) maxl = l;
+        S.maxlen = maxl;
+        uint64_t f = 0;
+        for (int l = (int)maxl - 1; l >= 1; l--) {
+            f = (f + S.count[l + 1] + 1) >> 1;
+            S.first[l] = f;
+        }
+        uint32_t e = 0;
+        for (uint32_t l = 1; l < HUFF_MAX_LEN; l++) {
+            e += S.count[l];
+            S.entry[l + 1] = e;
+        }
+    }
+    __syncthreads();
+    // slices of kCbThreads ids: a warp match ranks each id among the warp's ids
+    // of its length, a per-length scan over the warps (S.base carries the
+    // running base) gives its rank among this CTA's ids of that length
+    uint64_t tb = 0;
+    for (uint32_t sb = b0; sb < b1; sb += kCbThreads) {
+        __syncwarp();
+        for (uint32_t l = lane; l <= HUFF_MAX_LEN; l += 32) S.wcnt[warp][l] = 0;
+        __syncwarp();
+        const uint32_t id = sb + tid;
+        const uint32_t lm = id < b1 && !failed ? A.lenS[id] : 0u;
+        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, lm);
+        const uint32_t rank_w = __popc(peers & ((1u << lane) - 1));
+        if (rank_w == 0 && lm) S.wcnt[warp][lm] = __popc(peers);
+        __syncthreads();
+        for (uint32_t l = warp + 1; l <= S.maxlen; l += kCbThreads / 32) {
+            const uint32_t bl = S.base[l], cnt = S.wcnt[lane][l];
+            uint32_t inc = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            S.wcnt[lane][l] = bl + inc - cnt;
+            __syncwarp();
+            if (lane == 31) S.base[l] = bl + inc;
+        }
+        __syncthreads();
+        if (lm) {
+            const uint32_t rank = S.wcnt[warp][lm] + rank_w;
+            cw[id] = (S.first[lm] + rank) | ((uint64_t)lm << HUFF_CW_LEN_SHIFT);
+            sorted_syms[S.entry[lm] + rank] = id;
+            tb += (uint64_t)lm * g.hist[id];
+        } else if (id < b1) {
+            cw[id] = 0;
+        }
+        __syncthreads();
+    }
+    for (int o = 16; o; o >>= 1) tb += __shfl_xor_sync(0xFFFFFFFFu, tb, o);
+    if (lane == 0 && tb) atomicAdd((unsigned long long *)cl.map_shared_rank(&S.tb, 0), (unsigned long long)tb);
+    cl.sync();                                           // every CTA's bits are in; no remote access after this
+    if (R == 0) {
+        if (tid == 0) {
+            hdr->nbins = nbins;
+            hdr->max_len = S.maxlen;
+            uint32_t nu = 0;
+            for (uint32_t l = 1; l <= HUFF_MAX_LEN; l++) nu += S.count[l];
+            hdr->nused = nu;
+            hdr->status = failed ? HUFF_ERR_HIST_OVERFLOW : HUFF_OK;
+            hdr->total_bits = failed ? 0 : S.tb;
+            hdr->nsymbols = failed ? 0 : S.g_sum;
+        }
+        if (tid <= HUFF_MAX_LEN) {
+            hdr->first[tid] = S.first[tid];
+            hdr->entry[tid] = S.entry[tid];
+            hdr->count[tid] = S.count[tid];
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kCbThreads, 1) codebook_kernel(CbArgs g) {
     extern __shared__ __align__(16) uint8_t smem[];
     codebook_body<false>(g, g.nbins <= kCbSmemBins ? smem : g.scratch);
@@ -686,7 +1124,45 @@ huff_status codebook_batch_launch(const CbArgs *d_args, uint32_t nfields, uint32
 }
 
 size_t codebook_scratch_bytes(uint32_t nbins) {
+    if (nbins >= kCcMinBins) return cb_array_bytes(nbins) + cc_extra_bytes(nbins);
     return nbins <= kCbSmemBins ? 0 : cb_array_bytes(nbins);
+}
+
+// Cluster size for the cluster form on the current device: 16 where a
+// 16-CTA cluster of the kernel fits, else 8 (0: no cluster launch possible).
+static int cluster_size() {
+    static int cached[64];
+    static bool known[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    if (known[dev]) return cached[dev];
+    int best = 0;
+    for (int cl : {16, 8}) {
+        if (cl == 16 && cudaFuncSetAttribute(codebook_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed,
+                                             1) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(cl);
+        cfg.blockDim = dim3(kCbThreads);
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = cl;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, codebook_cluster_kernel, &cfg) == cudaSuccess && n >= 1) {
+            best = cl;
+            break;
+        }
+        cudaGetLastError();
+    }
+    cached[dev] = best;
+    known[dev] = true;
+    return best;
 }
 
 huff_status codebook_launch(const uint32_t *d_hist, uint32_t nbins, void *d_codebook, uint8_t *scratch,
@@ -697,6 +1173,25 @@ huff_status codebook_launch(const uint32_t *d_hist, uint32_t nbins, void *d_code
     a.book = static_cast<uint8_t *>(d_codebook);
     a.scratch = scratch;
     a.status = status;
+    if (nbins >= kCcMinBins) {
+        const int cl = cluster_size();
+        if (cl > 0) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(cl);
+            cfg.blockDim = dim3(kCbThreads);
+            cfg.stream = st;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = cl;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            if (cudaLaunchKernelEx(&cfg, codebook_cluster_kernel, a) != cudaSuccess) return HUFF_ERR_CUDA;
+            note_launch();
+            return HUFF_OK;
+        }
+    }
     if (nbins > kSmallAlphabet) {
         codebook_big_kernel<<<1, kCbThreads, 0, st>>>(a);
         note_launch();
