@@ -665,6 +665,7 @@ namespace cg = cooperative_groups;
 
 constexpr uint32_t kCcMinBins = 16385;     // alphabets from here on take the cluster form
 constexpr uint32_t kCcJumps = 7;           // pointer-jumping steps: depths up to 2^7
+constexpr uint32_t kCcBigRound = 4096;     // rounds melding at least this many pairs use the whole cluster
 
 // Scratch beyond CbArrays: parents and distances of the pointer jumping (two
 // buffers each, 2m entries) and the sorted leaves' symbol ids.
@@ -699,7 +700,55 @@ struct CcShared {
     uint32_t wcnt[kCbThreads / 32][HUFF_MAX_LEN + 1];
     uint64_t tb;                        // total bits (CTA 0 gathers the cluster's)
     uint32_t maxlen;
+    uint32_t rstate[4];                 // CTA 0's round state (c, ih, it, done), read by the cluster
+    uint32_t lstate[4];                 // this CTA's copy
 };
+
+// The selection of a GenerateCL round (the rule: codebook_body): the counts
+// mL, mI of waiting leaves and joined nodes it melds, in pairs.  Every warp
+// computes the same values from the same reads.
+__device__ __forceinline__ void round_select(const CbArrays &A, uint32_t m, uint32_t c, uint32_t ih, uint32_t it,
+                                             uint32_t &mL, uint32_t &mI) {
+    constexpr uint64_t kNone = 1ull << 33;
+    const uint64_t a0 = c < m ? A.wL[c] : kNone, a1 = c + 1 < m ? A.wL[c + 1] : kNone;
+    const uint64_t b0 = ih < it ? A.wI[ih] : kNone, b1 = ih + 1 < it ? A.wI[ih + 1] : kNone;
+    const uint64_t t = a0 <= b0 ? a0 + (a1 <= b0 ? a1 : b0) : b0 + (a0 <= b1 ? a0 : b1);
+    warp_upper_bound2(A.wL, c, m, A.wI, ih, it, (uint32_t)t, mL, mI);
+    mL -= c;
+    mI -= ih;
+    if ((mL + mI) & 1) {
+        const uint32_t lastI = mI ? A.wI[ih + mI - 1] : 0u, lastL = mL ? A.wL[c + mL - 1] : 0u;
+        const bool dropI = mI > 0 && (mL == 0 || lastI >= lastL);
+        if (dropI) mI--; else mL--;
+    }
+}
+
+// Melds pairs j0, j0 + stride, ... of a round (Merge Path co-ranking, leaf
+// first on equal weight), recording the joined weights and parent links.
+__device__ __forceinline__ void round_meld(const CbArrays &A, uint32_t m, uint32_t c, uint32_t ih, uint32_t it,
+                                           uint32_t mL, uint32_t mI, uint32_t j0, uint32_t stride) {
+    const uint32_t pairs = (mL + mI) >> 1;
+    const uint32_t *wa = A.wL + c, *wb = A.wI + ih;
+    for (uint32_t j = j0; j < pairs; j += stride) {
+        const uint32_t p = 2 * j;
+        uint32_t lo = p > mI ? p - mI : 0, hi = p < mL ? p : mL;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (wa[mid] <= wb[p - 1 - mid]) lo = mid + 1; else hi = mid;
+        }
+        uint32_t ia = lo, ib = p - lo, wsum = 0;
+        uint32_t node[2];
+#pragma unroll
+        for (int q = 0; q < 2; q++) {
+            const bool leaf = ia < mL && (ib >= mI || wa[ia] <= wb[ib]);
+            if (leaf) { node[q] = c + ia; wsum += wa[ia]; ia++; }
+            else { node[q] = m + ih + ib; wsum += wb[ib]; ib++; }
+        }
+        A.wI[it + j] = wsum;
+        A.parent[node[0]] = m + it + j;
+        A.parent[node[1]] = m + it + j;
+    }
+}
 
 // One stable counting pass of the cluster: elements [0, len), CTA R owning
 // [e0, e1); elem(i) gives the element (digit, payload); place(slot, payload)
@@ -891,54 +940,52 @@ __global__ void __launch_bounds__(kCbThreads, 1) codebook_cluster_kernel(CbArgs 
         }
         cl.sync();
 
-        // ---- GenerateCL rounds on CTA 0 (the rule and its proof: codebook_body)
-        if (R == 0) {
+        // ---- GenerateCL rounds (the rule and its proof: codebook_body).  CTA 0
+        // runs the rounds that meld fewer than kCcBigRound pairs alone (their
+        // cost is the latency of the round's chain); when the next round is
+        // larger it publishes the state, and the whole cluster melds that
+        // round, each CTA a share of the pairs, between two cluster barriers.
+        {
+            uint32_t c = 0, ih = 0, it = 0;
             const uint32_t rt = m <= 2048 ? 256u : (m <= 16384 ? 512u : (uint32_t)kCbThreads);
-            if (tid < rt) {
-                constexpr uint64_t kNone = 1ull << 33;
-                uint32_t c = 0, ih = 0, it = 0;
-                while ((m - c) + (it - ih) >= 2) {
-                    const uint64_t a0 = c < m ? A.wL[c] : kNone, a1 = c + 1 < m ? A.wL[c + 1] : kNone;
-                    const uint64_t bb0 = ih < it ? A.wI[ih] : kNone, bb1 = ih + 1 < it ? A.wI[ih + 1] : kNone;
-                    const uint64_t t = a0 <= bb0 ? a0 + (a1 <= bb0 ? a1 : bb0) : bb0 + (a0 <= bb1 ? a0 : bb1);
-                    uint32_t mL, mI;
-                    warp_upper_bound2(A.wL, c, m, A.wI, ih, it, (uint32_t)t, mL, mI);
-                    mL -= c;
-                    mI -= ih;
-                    if ((mL + mI) & 1) {
-                        const uint32_t lastI = mI ? A.wI[ih + mI - 1] : 0u, lastL = mL ? A.wL[c + mL - 1] : 0u;
-                        const bool dropI = mI > 0 && (mL == 0 || lastI >= lastL);
-                        if (dropI) mI--; else mL--;
+            for (;;) {
+                if (R == 0 && tid < rt) {
+                    while ((m - c) + (it - ih) >= 2) {
+                        uint32_t mL, mI;
+                        round_select(A, m, c, ih, it, mL, mI);
+                        const uint32_t pairs = (mL + mI) >> 1;
+                        if (pairs >= kCcBigRound && CL > 1) break;      // the cluster melds this one
+                        round_meld(A, m, c, ih, it, mL, mI, tid, rt);
+                        c += mL;
+                        ih += mI;
+                        it += pairs;
+                        asm volatile("bar.sync 1, %0;" ::"r"(rt) : "memory");
                     }
-                    const uint32_t pairs = (mL + mI) >> 1;
-                    const uint32_t *wa = A.wL + c, *wb = A.wI + ih;
-                    for (uint32_t j = tid; j < pairs; j += rt) {
-                        const uint32_t p = 2 * j;
-                        uint32_t lo = p > mI ? p - mI : 0, hi = p < mL ? p : mL;
-                        while (lo < hi) {
-                            const uint32_t mid = (lo + hi) >> 1;
-                            if (wa[mid] <= wb[p - 1 - mid]) lo = mid + 1; else hi = mid;
-                        }
-                        uint32_t ia = lo, ib = p - lo, wsum = 0;
-                        uint32_t node[2];
-#pragma unroll
-                        for (int q = 0; q < 2; q++) {
-                            const bool leaf = ia < mL && (ib >= mI || wa[ia] <= wb[ib]);
-                            if (leaf) { node[q] = c + ia; wsum += wa[ia]; ia++; }
-                            else { node[q] = m + ih + ib; wsum += wb[ib]; ib++; }
-                        }
-                        A.wI[it + j] = wsum;
-                        A.parent[node[0]] = m + it + j;
-                        A.parent[node[1]] = m + it + j;
+                    if (tid == 0) {
+                        S.rstate[0] = c;
+                        S.rstate[1] = ih;
+                        S.rstate[2] = it;
+                        S.rstate[3] = (m - c) + (it - ih) >= 2 ? 0u : 1u;
                     }
-                    c += mL;
-                    ih += mI;
-                    it += pairs;
-                    asm volatile("bar.sync 1, %0;" ::"r"(rt) : "memory");
                 }
+                cl.sync();                                   // CTA 0's rounds and state are out
+                if (tid < 4) S.lstate[tid] = *cl.map_shared_rank(&S.rstate[tid], 0);
+                __syncthreads();
+                c = S.lstate[0];
+                ih = S.lstate[1];
+                it = S.lstate[2];
+                const bool done = S.lstate[3] != 0;
+                __syncthreads();
+                if (done) break;
+                uint32_t mL, mI;
+                round_select(A, m, c, ih, it, mL, mI);
+                round_meld(A, m, c, ih, it, mL, mI, R * kCbThreads + tid, CL * kCbThreads);
+                c += mL;
+                ih += mI;
+                it += (mL + mI) >> 1;
+                cl.sync();                                   // the round's nodes are out; rstate read
             }
         }
-        cl.sync();
 
         // ---- depths by pointer jumping over the 2m - 1 nodes (root 2m - 2)
         const uint32_t nodes = 2 * m - 1, root = 2 * m - 2;
