@@ -644,7 +644,7 @@ __device__ __forceinline__ void codebook_body(const CbArgs &g, uint8_t *arrays) 
 
 // ---------------------------------------------------------------- cluster form
 //
-// Alphabets of more than kCcMinBins bins: one thread-block cluster of CL CTAs
+// Alphabets of kCcMinBins bins or more: one thread-block cluster of CL CTAs
 // (16 where the device allows it, else 8) builds the codebook.  The phases
 // whose work grows with the alphabet are split over the cluster's CTAs:
 //   sort      a stable LSD radix sort by count (8-bit digits); each CTA counts
@@ -663,7 +663,8 @@ __device__ __forceinline__ void codebook_body(const CbArgs &g, uint8_t *arrays) 
 
 namespace cg = cooperative_groups;
 
-constexpr uint32_t kCcMinBins = 16385;     // alphabets from here on take the cluster form
+constexpr uint32_t kCcMinBins = 4097;      // alphabets from here on take the cluster form (their arrays
+                                           // are in global memory anyway)
 constexpr uint32_t kCcJumps = 7;           // pointer-jumping steps: depths up to 2^7
 constexpr uint32_t kCcBigRound = 4096;     // rounds melding at least this many pairs use the whole cluster
 
