@@ -97,7 +97,7 @@ __device__ __noinline__ uint32_t decode_long(uint64_t win, uint32_t L, uint32_t 
 // first invalid code; reports it, and a chunk that does not end exactly at
 // pend, through the status word.  Reads are bounded by the stream and writes
 // by the chunk, whatever the stream holds.
-template <int W>
+template <int W, bool FMT>
 __device__ __forceinline__ void decode_chunk(const DecArgs &a, const uint32_t *gsyms, bool pair, uint32_t L,
                                              uint32_t max_len, uint64_t i0, uint64_t i1, uint64_t p0, uint64_t pend) {
     using Sym = typename std::conditional<W == 1, uint8_t, typename std::conditional<W == 2, uint16_t, uint32_t>::type>::type;
@@ -113,8 +113,13 @@ __device__ __forceinline__ void decode_chunk(const DecArgs &a, const uint32_t *g
     const uint32_t *cin = a.in + cw0;
     const uint64_t left = a.in_words > cw0 ? a.in_words - cw0 : 0;
     const uint32_t lim = left < 0xFFFFFFFFull ? (uint32_t)left : 0xFFFFFFFFu;
-    const uint32_t perm = a.perm;
-    auto word = [&](uint32_t k) { return k < lim ? __byte_perm(__ldg(cin + k), 0u, perm) : 0u; };
+    // FMT: a stream of 8- or 16-bit units or the chunk-aligned layout (words
+    // permuted into stream order, offsets in units, padded chunk ends)
+    const uint32_t perm = FMT ? a.perm : 0x3210u;
+    auto word = [&](uint32_t k) {
+        const uint32_t w = k < lim ? __ldg(cin + k) : 0u;
+        return FMT ? __byte_perm(w, 0u, perm) : w;
+    };
     uint32_t hi, lo, nb, wn, nxt;
     auto start = [&](uint64_t p) {
         wn = (uint32_t)((p >> 5) - cw0);
@@ -153,7 +158,7 @@ __device__ __forceinline__ void decode_chunk(const DecArgs &a, const uint32_t *g
             // the buffer when it holds max_len bits, else on a fresh window
             uint32_t r = 0;
             if (e == 0) {
-                const uint64_t win = max_len <= nb ? ((uint64_t)hi << 32 | lo) : window64(a.in, a.in_words, pos(), a.perm);
+                const uint64_t win = max_len <= nb ? ((uint64_t)hi << 32 | lo) : window64(a.in, a.in_words, pos(), perm);
                 r = decode_long(win, L, max_len, gsyms);
             }
             if (r == 0) { ok = false; return; }
@@ -247,11 +252,12 @@ __device__ __forceinline__ void decode_chunk(const DecArgs &a, const uint32_t *g
     // dense: the chunk ends exactly at the next offset; chunk-aligned: within
     // the unit before it (the rest of that unit is padding)
     const uint64_t pe = pos();
-    if (!ok || pe > pend || ((pe + a.unit_mask) & ~(uint64_t)a.unit_mask) != pend)
+    const uint64_t um = FMT ? a.unit_mask : 0u;
+    if (!ok || pe > pend || ((pe + um) & ~um) != pend)
         set_error(a.status, HUFF_ERR_INVALID_ARG);
 }
 
-template <int W>
+template <int W, bool FMT>
 __global__ void __launch_bounds__(kDecThreads) decode_kernel(DecArgs a) {
     const huff_codebook_header *hdr = reinterpret_cast<const huff_codebook_header *>(a.book);
     const uint32_t *sorted_syms = reinterpret_cast<const uint32_t *>(a.book + cb_sorted_offset(a.nbins));
@@ -361,8 +367,8 @@ __global__ void __launch_bounds__(kDecThreads) decode_kernel(DecArgs a) {
     for (uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; c < a.nchunks; c += stride) {
         const uint64_t i0 = c << a.chunk_log2;
         const uint64_t i1 = i0 + (1ull << a.chunk_log2) < a.n ? i0 + (1ull << a.chunk_log2) : a.n;
-        decode_chunk<W>(a, sorted_syms, pair, L, max_len, i0, i1, a.offs[c] << a.off_shift,
-                        a.offs[c + 1] << a.off_shift);
+        const uint32_t osh = FMT ? a.off_shift : 0u;
+        decode_chunk<W, FMT>(a, sorted_syms, pair, L, max_len, i0, i1, a.offs[c] << osh, a.offs[c + 1] << osh);
     }
 }
 
@@ -394,7 +400,11 @@ huff_status decode_launch(const void *d_in, uint64_t total_bits, const uint64_t 
                  a.nchunks <= (uint64_t)sm_count() * kDecThreads;
     a.status = status;
     if (a.nchunks == 0) return HUFF_OK;
-    void (*kern)(DecArgs) = dtype == HUFF_U8 ? decode_kernel<1> : dtype == HUFF_U16 ? decode_kernel<2> : decode_kernel<4>;
+    void (*kern)(DecArgs);
+    if (format == 0)
+        kern = dtype == HUFF_U8 ? decode_kernel<1, false> : dtype == HUFF_U16 ? decode_kernel<2, false> : decode_kernel<4, false>;
+    else
+        kern = dtype == HUFF_U8 ? decode_kernel<1, true> : dtype == HUFF_U16 ? decode_kernel<2, true> : decode_kernel<4, true>;
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kDecThreads, 0);
     if (occ < 1) occ = 1;
