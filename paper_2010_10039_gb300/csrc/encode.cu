@@ -1,7 +1,7 @@
 // Single-field encode launch (huff_encode, huff_encode_noalloc): the kernel
 // of encode_impl.cuh over one field whose codebook-derived tile layout the
 // kernel works out itself.
-#include "encode_impl.cuh"
+#include "encode_seg.cuh"
 
 namespace huff {
 
@@ -77,17 +77,29 @@ static huff_status launch_encode(const void *d_sym, uint64_t n, const void *d_co
         note_launch();
         a.etab = etab;
     }
-    const size_t smem = enc_smem_bytes<Sym>(gtab, a.tslots, 0);
-    void (*kern)(EncArgs) = fmt_chunk_aligned(format) ? encode_kernel_aligned<Sym>(gtab)
-                            : gtab ? encode_kernel<Sym, true, false> : encode_kernel<Sym, false, false>;
+    size_t smem = enc_smem_bytes<Sym>(gtab, a.tslots, 0);
+    void (*kern)(EncArgs);
+    int threads = kEncCtaThreads;
+    if (fmt_chunk_aligned(format)) {
+        kern = encode_kernel_aligned<Sym>(gtab);
+    } else if (!gtab || a.etab) {
+        // the segment path when the codebook allows it (decided on the device),
+        // else the general encoder: room for either layout
+        kern = encode_one_kernel_get<Sym>(gtab);
+        threads = kSegThreads;
+        const size_t seg = seg_smem_bytes<Sym>(a.tslots, gtab);
+        if (seg > smem) smem = seg;
+    } else {
+        kern = encode_kernel<Sym, true, false>;
+    }
     if (!allow_dynamic_smem((const void *)kern, smem))
         return HUFF_ERR_CUDA;
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kEncCtaThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
     if (occ < 1) occ = 1;
     uint64_t grid = (uint64_t)sm_count() * occ;
     if (grid > max_tiles) grid = max_tiles;
-    kern<<<(unsigned)grid, kEncCtaThreads, smem, st>>>(a);
+    kern<<<(unsigned)grid, threads, smem, st>>>(a);
     note_launch();
     return cudaGetLastError() == cudaSuccess ? HUFF_OK : HUFF_ERR_CUDA;
 }

@@ -1013,15 +1013,15 @@ __host__ __device__ inline size_t enc_smem_bytes(bool gtab, uint32_t tslots, uin
            (nfields_batch ? 4ull * (nfields_batch + 1) : 0);
 }
 
-template <typename Sym, bool GTAB, bool BATCH, bool CALIGN = false>
-__global__ void __launch_bounds__(kEncCtaThreads, sizeof(Sym) == 1 ? 2 : 3) encode_kernel(EncArgs a) {
-    extern __shared__ __align__(128) uint8_t smem[];
+// The kernel body over the dynamic shared memory smem (stages, bit ring,
+// codebook table, batch tile bases) and the launch's EncShared record.
+template <typename Sym, bool GTAB, bool BATCH, bool CALIGN>
+__device__ __forceinline__ void encode_body(const EncArgs &a, uint8_t *smem, EncShared &S) {
     constexpr uint32_t RW = ring_words<Sym>();
     uint8_t *stage = smem;
     uint32_t *ring = reinterpret_cast<uint32_t *>(smem + kEncStages * kEncSubBytes);
     uint64_t *tab = reinterpret_cast<uint64_t *>(ring + RW);
     uint32_t *tbase = reinterpret_cast<uint32_t *>(reinterpret_cast<uint8_t *>(tab) + (GTAB ? 0 : a.tslots * 8ull));
-    __shared__ EncShared S;
 
     uint32_t total, nsub1 = 0, max_len1 = 0;
     int r;
@@ -1033,7 +1033,7 @@ __global__ void __launch_bounds__(kEncCtaThreads, sizeof(Sym) == 1 ? 2 : 3) enco
         r = c.r;
         e32 = c.entry32 != 0;
         fields = a.fields;
-        for (uint32_t i = threadIdx.x; i <= a.nfields; i += blockDim.x)
+        for (uint32_t i = threadIdx.x; i <= a.nfields; i += kEncCtaThreads)
             tbase[i] = i < a.nfields ? a.fields[i].tile_base : total;
     } else {
         const huff_codebook_header *hdr = reinterpret_cast<const huff_codebook_header *>(a.one.book);
@@ -1060,7 +1060,7 @@ __global__ void __launch_bounds__(kEncCtaThreads, sizeof(Sym) == 1 ? 2 : 3) enco
         }
         fields = &S.f0;
     }
-    for (uint32_t i = threadIdx.x; i < RW; i += blockDim.x) ring[i] = 0;
+    for (uint32_t i = threadIdx.x; i < RW; i += kEncCtaThreads) ring[i] = 0;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kEncStages; s++) mbar_init(&S.bars[s], 1);
         for (int b = 0; b < kSlots; b++) {
@@ -1071,7 +1071,8 @@ __global__ void __launch_bounds__(kEncCtaThreads, sizeof(Sym) == 1 ? 2 : 3) enco
         S.ring_tail = 0;
         fence_barrier_init();
     }
-    __syncthreads();
+    // the kernel's first kEncCtaThreads threads (a launch may have more, idle)
+    asm volatile("bar.sync 2, %0;" ::"n"(kEncCtaThreads) : "memory");
     if (threadIdx.x >= kEncThreads + 32) {
         writeout_loop<Sym>(fields, ring, total, S);
         return;
@@ -1100,6 +1101,13 @@ __global__ void __launch_bounds__(kEncCtaThreads, sizeof(Sym) == 1 ? 2 : 3) enco
         merge_dispatch<Sym, uint64_t, kTab, BATCH, CALIGN>(r, a, fields, tbase, stage, ring, GTAB ? nullptr : tab, total, nsub1,
                                                    max_len1, S);
     }
+}
+
+template <typename Sym, bool GTAB, bool BATCH, bool CALIGN = false>
+__global__ void __launch_bounds__(kEncCtaThreads, sizeof(Sym) == 1 ? 2 : 3) encode_kernel(EncArgs a) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    __shared__ EncShared S;
+    encode_body<Sym, GTAB, BATCH, CALIGN>(a, smem, S);
 }
 
 // The single-field kernel with the chunk-aligned layout's padding in the

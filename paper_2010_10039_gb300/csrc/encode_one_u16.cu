@@ -1,0 +1,15 @@
+// Single-field encode kernels for uint16 symbols (the segment path with the
+// general encoder as its fallback), in a translation unit of their own so the
+// three symbol widths compile in parallel.
+#include "encode_seg.cuh"
+
+namespace huff {
+
+template <typename Sym>
+EncOneFn encode_one_kernel_get(bool gtab) {
+    return gtab ? encode_one_kernel<Sym, true> : encode_one_kernel<Sym, false>;
+}
+
+template EncOneFn encode_one_kernel_get<uint16_t>(bool);
+
+}  // namespace huff
