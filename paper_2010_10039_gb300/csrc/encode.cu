@@ -18,12 +18,11 @@ size_t encode_scratch_bytes(uint64_t n, uint32_t nbins) {
 
 // The codebook's 32-bit table entries (code << (32 - l) | l), precomputed once
 // per launch when the codebook stays in global memory: a lookup then reads one
-// word instead of converting a 64-bit codeword.  Codes over 23 bits keep the
-// 64-bit codewords (the encoder then ignores this table).  Measured on u32
-// Zipf fields: 8,192 entries (32 KB, within L1) took the encode from 300 to
-// 244 us; 65,536 entries (256 KB, beyond L1) were slower than converting the
-// codewords (435 against 352 us), so larger alphabets keep the codewords.
-constexpr uint32_t kEncEntryTableBins = 16384;
+// word instead of converting a 64-bit codeword, and the segment path, which
+// takes only 32-bit entries, can run.  Codes over 23 bits keep the 64-bit
+// codewords (the encoder then ignores this table).  Up to 65,536 entries (the
+// allocation-free entry point's array holds that many).
+constexpr uint32_t kEncEntryTableBins = 65536;
 __global__ void entry_table_kernel(const uint8_t *book, uint32_t nbins, uint32_t *etab) {
     const huff_codebook_header *hdr = reinterpret_cast<const huff_codebook_header *>(book);
     if (hdr->max_len > 23) return;
