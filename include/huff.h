@@ -98,8 +98,10 @@ typedef struct {
                               -1 = pick r from the average codeword length (Sec. IV-C rule,
                               as huff_reduce_factor with 32-bit words).  Whatever r is asked
                               for or ruled, the scan encoder then clamps it to what its
-                              registers allow: [2, 4] for u8, [2, 3] for u16, [0, 2] for u32;
-                              the shuffle encoder takes r as given (<= 4; -1 = 3, fixed)      */
+                              registers allow: [2, 4] for u8, [2, 3] for u16, and for u32
+                              [1, 2] on its segment path (codes of at most 23 bits), [0, 2]
+                              otherwise; the shuffle encoder takes r as given (<= 4; -1 = 3,
+                              fixed).  r never changes the output                             */
     int32_t block_threads; /* reserved: the encoders' CTA shapes are fixed per dtype (the
                               autotuner of the batched form picks CTAs per SM); any value is
                               accepted and ignored                                            */
