@@ -981,9 +981,10 @@ __host__ __device__ inline int enc_clamp_r(int r) {
 }
 
 // Reduction factor rule of Sec. IV-C: floor(log2 beta) + r + 1 = log2(W)
-// (W = 2^wlog, the typed unit), beta = total_bits / nsymbols the average
-// codeword length, clamped to [0, wlog] like huff_reduce_factor (the caller
-// then applies the register clamp).
+// (W = 2^wlog), beta = total_bits / nsymbols the average codeword length,
+// clamped to [0, wlog] like huff_reduce_factor (the caller then applies the
+// register clamp).  The encoders take W = 32, the word their runs are merged
+// into, for every stored unit width.
 __host__ __device__ inline int enc_rule_r(uint64_t total_bits, uint64_t nsymbols, int wlog = 5) {
     // floor(log2(beta)): largest f with nsymbols * 2^f <= total_bits
     int f = 0;
@@ -1046,8 +1047,7 @@ __device__ __forceinline__ void encode_body(const EncArgs &a, uint8_t *smem, Enc
         const uint32_t nsub = enc_subs_per_tile<Sym>(max_len, a.nsub_cap);
         const uint64_t TILE = (uint64_t)enc_sub_syms<Sym>() * nsub;
         total = (uint32_t)((a.one.n + TILE - 1) / TILE);
-        r = enc_clamp_r<Sym>(a.reduce_log2 >= 0 ? a.reduce_log2
-                                                : enc_rule_r(hdr->total_bits, hdr->nsymbols, (int)fmt_wlog(a.one.format)));
+        r = enc_clamp_r<Sym>(a.reduce_log2 >= 0 ? a.reduce_log2 : enc_rule_r(hdr->total_bits, hdr->nsymbols));
         e32 = max_len <= 23;
         nsub1 = nsub;
         max_len1 = max_len;

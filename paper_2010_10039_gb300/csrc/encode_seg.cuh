@@ -755,8 +755,9 @@ __device__ __forceinline__ void seg_body(const EncArgs &a, uint8_t *smem, SegSha
         seg_helper<Sym>(a, T.f0, ring, total, T, (threadIdx.x - kEncThreads) / 32);
         return;
     }
-    int r = a.reduce_log2 >= 0 ? a.reduce_log2
-                               : enc_rule_r(hdr->total_bits, hdr->nsymbols, (int)fmt_wlog(a.one.format));
+    // the rule's word is the 32-bit ring word the runs are merged into, whatever
+    // unit the stream is stored in
+    int r = a.reduce_log2 >= 0 ? a.reduce_log2 : enc_rule_r(hdr->total_bits, hdr->nsymbols);
     r = r < seg_r_min<Sym>() ? seg_r_min<Sym>() : (r > seg_r_max<Sym>() ? seg_r_max<Sym>() : r);
     const bool many = (1ull << a.one.chunk_log2) < (uint64_t)seg_lane_syms<Sym>();
     if (GTAB) seg_merge_r<Sym, 2>(r, many, a, stage, ring, a.etab, total, T);

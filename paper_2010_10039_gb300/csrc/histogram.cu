@@ -4,8 +4,8 @@
 // atomics and finally folds the replicas into the global histogram.
 //
 // GB300 form: a persistent grid streams the input in CTA-contiguous 16 KB
-// rounds; each thread issues two independent 16-byte loads per round, so the
-// ~6.8 TB/s of HBM3e sees enough bytes in flight with two CTAs per SM.  Each
+// rounds; each thread issues two independent 16-byte loads per round, and
+// loads the next round's pair before it counts the current one.  Each
 // warp counts into its own replica (same-bin conflicts stay inside one warp),
 // the replicas are folded once per CTA and only nonzero bins reach the global
 // histogram.  Alphabets too large for 32-bit counters in shared memory use
@@ -182,15 +182,30 @@ __global__ void __launch_bounds__(hist_threads(PACKED), PACKED ? 1 : 2) hist_ker
     const Carry cy{a.hist, a.nbins};
     const uint64_t nrounds = (a.nvec + kRound - 1) / kRound;
     uint32_t since = 0;
+    uint4 v0 = make_uint4(0u, 0u, 0u, 0u), v1 = v0;
+    if (blockIdx.x < nrounds) {
+        const uint64_t i0 = blockIdx.x * kRound + threadIdx.x, i1 = i0 + T;
+        if (i0 < a.nvec) v0 = vec[i0];
+        if (i1 < a.nvec) v1 = vec[i1];
+    }
     for (uint64_t r = blockIdx.x; r < nrounds; r += gridDim.x) {
         const uint64_t i0 = r * kRound + threadIdx.x, i1 = i0 + T;
+        // the next round's vectors are loaded before this round is counted
+        uint4 n0 = v0, n1 = v1;
+        const uint64_t rn = r + gridDim.x;
+        if (rn < nrounds) {
+            const uint64_t j0 = rn * kRound + threadIdx.x, j1 = j0 + T;
+            if (j0 < a.nvec) n0 = vec[j0];
+            if (j1 < a.nvec) n1 = vec[j1];
+        }
         if (i1 < a.nvec) {
-            uint4 v0 = vec[i0], v1 = vec[i1];
             count_vec<Sym, PACKED, PACKED>(my, v0, mask, seen, cy, &bad);
             count_vec<Sym, PACKED, PACKED>(my, v1, mask, seen, cy, &bad);
         } else if (i0 < a.nvec) {
-            count_vec<Sym, PACKED, PACKED>(my, vec[i0], mask, seen, cy, &bad);
+            count_vec<Sym, PACKED, PACKED>(my, v0, mask, seen, cy, &bad);
         }
+        v0 = n0;
+        v1 = n1;
         if (PACKED && ++since == kRoundsPerEpoch) {
             __syncthreads();
             since = 0;
