@@ -330,6 +330,11 @@ typedef struct {
                                length (used when not tuning)                                            */
     int32_t max_subtiles;   /* sub-tiles per encode tile, 1..8; 0 = 8 (used when not tuning)             */
     int32_t ctas_per_sm;    /* encode CTAs per SM; 0 = as many as fit (used when not tuning)            */
+    int32_t per_field;      /* 0: the encode stage is one persistent launch over all fields of a group;
+                               1: one single-field encode launch per field (as huff_encode: the segment
+                               encoder where a field's codewords allow it), run concurrently on the
+                               plan's side streams inside the graph; r as above, the sub-tile and CTA
+                               settings then unused (used when not tuning; the tuner times both)      */
 } huff_batch_cfg;
 
 typedef struct {
@@ -342,11 +347,13 @@ typedef struct {
     uint32_t candidates;     /* settings timed by the tuner (0: not tuned)                        */
     float tuned_ms;          /* best time of one batch during tuning                              */
     uint64_t device_bytes;   /* device memory held by the plan                                    */
+    uint32_t per_field;      /* encode form in use (huff_batch_cfg.per_field)                     */
+    uint32_t per_field_tiles;/* per-field form: least tiles per CTA of each launch (0: not in use)  */
 } huff_batch_info;
 
 typedef struct huff_batch_plan huff_batch_plan;
 
-/* Default configuration: autotune off, r by rule, 8 sub-tiles, CTAs that fit. */
+/* Default configuration: autotune off, r by rule, 8 sub-tiles, CTAs that fit, one persistent encode launch. */
 void huff_batch_default_cfg(huff_batch_cfg *cfg);
 
 /*

@@ -2,6 +2,10 @@
 // layout, capture of the launch set in a CUDA graph, and the autotuner that
 // picks the encoder's reduction factor, tile size, CTAs per SM and (for
 // fields that leave it open) chunk size by timing the graph on the fields.
+// The encode stage takes one of two forms: one persistent launch whose tiles
+// run over all fields of a group, or one single-field launch per field (the
+// segment encoder wherever the field's codewords allow it), fanned out over
+// side streams inside the graph; the tuner times both.
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -16,6 +20,11 @@ void launch_count_suppress(bool on);
 constexpr uint32_t kGroupMaxFields = 512;     // encode keeps one first-tile id per field in shared memory
 constexpr uint32_t kMaxBatchFields = 65536;
 constexpr int kAutoChunkLog2[3] = {10, 12, 14};
+#ifndef HUFF_BATCH_SIDE_STREAMS
+#define HUFF_BATCH_SIDE_STREAMS 64
+#endif
+constexpr int kSideStreams = HUFF_BATCH_SIDE_STREAMS;   // per-field encode launches run on these, concurrently
+constexpr int kPerFieldTiles[3] = {8, 16, 32};          // tuner: least tiles per CTA of a per-field launch
 
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -33,6 +42,9 @@ struct BatchGroup {
     size_t escr_bytes = 0, cbscr_stride = 0;
     uint32_t grid_h = 1, grid_c = 1;
     int enc_occ = 1;                    // encode CTAs per SM that fit
+    size_t off_fscr = 0, fscr_bytes = 0;
+    std::vector<size_t> fscr;           // per field: its single-field encode scratch, from off_fscr
+    std::vector<uint32_t> by_size;      // field positions, most symbols first
 };
 
 struct Setting {
@@ -40,6 +52,7 @@ struct Setting {
     int max_subtiles;
     int ctas_per_sm;    // 0 = as many as fit
     int chunk_log2;     // M for fields created with -1
+    int per_field;      // k >= 1: one single-field encode launch per field, at least k tiles per CTA
 };
 
 }  // namespace huff
@@ -57,6 +70,9 @@ struct huff_batch_plan {
     uint8_t *dmem = nullptr;
     size_t dbytes = 0;
     cudaStream_t cs = nullptr;          // capture / tuning stream
+    cudaStream_t side[kSideStreams] = {};
+    cudaEvent_t fork = nullptr;
+    cudaEvent_t join[kSideStreams] = {};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     Setting cur{};
@@ -105,6 +121,43 @@ huff_status apply_chunks(huff_batch_plan *p, int auto_m) {
     return cudaStreamSynchronize(p->cs) == cudaSuccess ? HUFF_OK : HUFF_ERR_CUDA;
 }
 
+// The encode stage as one single-field launch per field (its scratch cleared
+// already): fanned out from st over the side streams, each field to the
+// stream with the fewest symbols so far (largest fields first), and joined
+// back into st.
+huff_status encode_fields(huff_batch_plan *p, const BatchGroup &g, const Setting &s, cudaStream_t st) {
+    const int ns = (int)std::min<size_t>(kSideStreams, g.idx.size());
+    if (cudaEventRecord(p->fork, st) != cudaSuccess) return HUFF_ERR_CUDA;
+    for (int k = 0; k < ns; k++)
+        if (cudaStreamWaitEvent(p->side[k], p->fork, 0) != cudaSuccess) return HUFF_ERR_CUDA;
+    uint64_t load[kSideStreams] = {};
+    for (uint32_t fi : g.by_size) {
+        int k = 0;
+        for (int j = 1; j < ns; j++)
+            if (load[j] < load[k]) k = j;
+        const uint32_t i = g.idx[fi];
+        const huff_field &f = p->fields[i];
+        load[k] += f.n + 1;
+        if (f.n == 0) {
+            if (cudaMemsetAsync(f.d_chunk_bit_offset, 0, 8, p->side[k]) != cudaSuccess ||
+                cudaMemsetAsync(f.d_total_bits, 0, 8, p->side[k]) != cudaSuccess)
+                return HUFF_ERR_CUDA;
+            continue;
+        }
+        const huff_status e = encode_launch_ex(f.d_sym, f.n, f.dtype, p->dmem + p->off_book[i], f.nbins,
+                                               p->chunk_log2[i], s.r, 0u, static_cast<uint32_t *>(f.d_out),
+                                               f.out_capacity_words, f.d_chunk_bit_offset, f.d_total_bits,
+                                               p->dmem + g.off_fscr + g.fscr[fi], status_ptr(p, i), p->side[k], 0u,
+                                               0u, true, (uint32_t)s.per_field);
+        if (e != HUFF_OK) return e;
+    }
+    for (int k = 0; k < ns; k++) {
+        if (cudaEventRecord(p->join[k], p->side[k]) != cudaSuccess) return HUFF_ERR_CUDA;
+        if (cudaStreamWaitEvent(st, p->join[k], 0) != cudaSuccess) return HUFF_ERR_CUDA;
+    }
+    return HUFF_OK;
+}
+
 // The launch set of one batch run, enqueued on st (captured into the graph).
 // With ev (5 events per group), events are recorded around each stage.
 huff_status record(huff_batch_plan *p, const Setting &s, cudaStream_t st, const cudaEvent_t *ev = nullptr) {
@@ -129,6 +182,15 @@ huff_status record(huff_batch_plan *p, const Setting &s, cudaStream_t st, const 
         e = codebook_batch_launch(reinterpret_cast<const CbArgs *>(p->dmem + g.off_cb), nf, g.max_nbins, g.grid_c,
                                   g.cbscr_stride ? p->dmem + g.off_cbscr : nullptr, g.cbscr_stride, st);
         if (e != HUFF_OK) return e;
+        if (s.per_field) {
+            if (!mark(2)) return HUFF_ERR_CUDA;
+            if (cudaMemsetAsync(p->dmem + g.off_fscr, 0, g.fscr_bytes, st) != cudaSuccess) return HUFF_ERR_CUDA;
+            if (!mark(3)) return HUFF_ERR_CUDA;
+            if ((e = encode_fields(p, g, s, st)) != HUFF_OK) return e;
+            if (!mark(4)) return HUFF_ERR_CUDA;
+            gi++;
+            continue;
+        }
         EncField *ef = reinterpret_cast<EncField *>(p->dmem + g.off_ef);
         EncBatchConf *conf = reinterpret_cast<EncBatchConf *>(p->dmem + g.off_conf);
         if (!mark(2)) return HUFF_ERR_CUDA;
@@ -144,6 +206,21 @@ huff_status record(huff_batch_plan *p, const Setting &s, cudaStream_t st, const 
         gi++;
     }
     return HUFF_OK;
+}
+
+// Kernel launches of one run in the plan's current setting.
+uint32_t count_kernels(const huff_batch_plan *p) {
+    uint32_t k = 0;
+    for (const BatchGroup &g : p->groups) {
+        k += (g.tiles.empty() ? 0 : 1) + 1;                 // histogram, codebooks
+        if (!p->cur.per_field) {
+            k += 2;                                          // tile planner, encode
+            continue;
+        }
+        for (uint32_t i : g.idx)
+            if (p->fields[i].n) k += encode_kernels_per_call(p->fields[i].nbins);
+    }
+    return k;
 }
 
 void drop_graph(huff_batch_plan *p) {
@@ -212,7 +289,7 @@ huff_status autotune(huff_batch_plan *p) {
     }
     const bool any_auto = std::find(p->auto_chunk.begin(), p->auto_chunk.end(), 1) != p->auto_chunk.end();
     std::vector<int> ms_list = any_auto ? std::vector<int>(kAutoChunkLog2, kAutoChunkLog2 + 3) : std::vector<int>{0};
-    Setting best{-1, 8, 0, any_auto ? 10 : 0};
+    Setting best{-1, 8, 0, any_auto ? 10 : 0, 0};
     float best_ms = 1e30f;
     uint32_t count = 0;
     huff_status e0 = apply_chunks(p, 10);
@@ -220,7 +297,7 @@ huff_status autotune(huff_batch_plan *p) {
     for (int r = rmin; r <= rmax; r++)
         for (int cap : {2, 4, 8})
             for (int c = 1; c <= std::min(occ, 3); c++) {
-                Setting s{r, cap, c, 0};
+                Setting s{r, cap, c, 0, 0};
                 huff_status e = capture(p, s);
                 if (e != HUFF_OK) return e;
                 for (int m : ms_list) {
@@ -235,6 +312,23 @@ huff_status autotune(huff_batch_plan *p) {
                     }
                 }
             }
+    // one launch per field (r by rule: on the segment path r moves the time little)
+    for (int per : kPerFieldTiles) {
+        const Setting s{-1, 8, 0, 0, per};
+        huff_status e = capture(p, s);
+        if (e != HUFF_OK) return e;
+        for (int m : ms_list) {
+            if (any_auto && (e = apply_chunks(p, m)) != HUFF_OK) return e;
+            float t;
+            if ((e = time_graph(p, 3, &t)) != HUFF_OK) return e;
+            count++;
+            if (t < best_ms) {
+                best_ms = t;
+                best = s;
+                best.chunk_log2 = m;
+            }
+        }
+    }
     p->candidates = count;
     p->tuned_ms = best_ms;
     p->cur = best;
@@ -248,9 +342,16 @@ huff_status autotune(huff_batch_plan *p) {
 void free_plan(huff_batch_plan *p) {
     if (!p) return;
     if (p->cs) cudaStreamSynchronize(p->cs);
+    for (cudaStream_t s : p->side)
+        if (s) cudaStreamSynchronize(s);
     drop_graph(p);
     if (p->dmem) cudaFree(p->dmem);
     if (p->cs) cudaStreamDestroy(p->cs);
+    for (cudaStream_t s : p->side)
+        if (s) cudaStreamDestroy(s);
+    if (p->fork) cudaEventDestroy(p->fork);
+    for (cudaEvent_t e : p->join)
+        if (e) cudaEventDestroy(e);
     delete p;
 }
 
@@ -264,6 +365,7 @@ void huff_batch_default_cfg(huff_batch_cfg *cfg) {
     cfg->reduce_log2 = -1;
     cfg->max_subtiles = 0;
     cfg->ctas_per_sm = 0;
+    cfg->per_field = 0;
 }
 
 huff_status huff_batch_plan_create(const huff_field *fields, uint32_t nfields, const huff_batch_cfg *cfg,
@@ -274,7 +376,8 @@ huff_status huff_batch_plan_create(const huff_field *fields, uint32_t nfields, c
     huff_batch_cfg c;
     huff_batch_default_cfg(&c);
     if (cfg) c = *cfg;
-    if (c.reduce_log2 < -1 || c.reduce_log2 > 4 || c.max_subtiles < 0 || c.max_subtiles > 8 || c.ctas_per_sm < 0)
+    if (c.reduce_log2 < -1 || c.reduce_log2 > 4 || c.max_subtiles < 0 || c.max_subtiles > 8 || c.ctas_per_sm < 0 ||
+        (c.per_field != 0 && c.per_field != 1))
         return HUFF_ERR_INVALID_ARG;
     for (uint32_t i = 0; i < nfields; i++)
         if (!field_ok(fields[i])) return HUFF_ERR_INVALID_ARG;
@@ -338,11 +441,25 @@ huff_status huff_batch_plan_create(const huff_field *fields, uint32_t nfields, c
         g.off_conf = take(sizeof(EncBatchConf));
         g.escr_bytes = 64 + 16 * max_tiles;
         g.off_escr = take(g.escr_bytes);
+        size_t fs = 0;
+        for (uint32_t fi = 0; fi < g.idx.size(); fi++) {
+            const huff_field &f = fields[g.idx[fi]];
+            g.fscr.push_back(fs);
+            fs += align_up(encode_scratch_bytes(f.n, f.nbins), 256);
+        }
+        g.fscr_bytes = std::max<size_t>(fs, 256);
+        g.off_fscr = take(g.fscr_bytes);
+        g.by_size.resize(g.idx.size());
+        for (uint32_t fi = 0; fi < g.idx.size(); fi++) g.by_size[fi] = fi;
+        std::stable_sort(g.by_size.begin(), g.by_size.end(),
+                         [&](uint32_t a, uint32_t b) { return fields[g.idx[a]].n > fields[g.idx[b]].n; });
         // launch shapes (attributes are set here, before any capture)
         int occ_h = 1, occ_c = 1;
         huff_status e = histogram_batch_prepare(g.dtype, g.max_nbins, &occ_h);
         if (e == HUFF_OK) e = codebook_batch_prepare(g.max_nbins, &occ_c);
         if (e == HUFF_OK) e = encode_batch_prepare(g.dtype, g.max_nbins, (uint32_t)g.idx.size(), &g.enc_occ);
+        for (uint32_t fi = 0; fi < g.idx.size() && e == HUFF_OK; fi++)
+            e = encode_prepare(g.dtype, fields[g.idx[fi]].nbins);
         if (e != HUFF_OK) {
             free_plan(p);
             return e;
@@ -362,6 +479,21 @@ huff_status huff_batch_plan_create(const huff_field *fields, uint32_t nfields, c
     }
     if (cudaStreamCreateWithFlags(&p->cs, cudaStreamNonBlocking) != cudaSuccess) {
         p->cs = nullptr;
+        free_plan(p);
+        return HUFF_ERR_CUDA;
+    }
+    bool made = cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming) == cudaSuccess;
+    if (!made) p->fork = nullptr;
+    for (int k = 0; k < kSideStreams && made; k++) {
+        if (cudaStreamCreateWithFlags(&p->side[k], cudaStreamNonBlocking) != cudaSuccess) {
+            p->side[k] = nullptr;
+            made = false;
+        } else if (cudaEventCreateWithFlags(&p->join[k], cudaEventDisableTiming) != cudaSuccess) {
+            p->join[k] = nullptr;
+            made = false;
+        }
+    }
+    if (!made) {
         free_plan(p);
         return HUFF_ERR_CUDA;
     }
@@ -410,14 +542,12 @@ huff_status huff_batch_plan_create(const huff_field *fields, uint32_t nfields, c
             return HUFF_ERR_CUDA;
         }
     }
-    p->kernels_per_run = 0;
-    for (const BatchGroup &g : p->groups) p->kernels_per_run += (g.tiles.empty() ? 0 : 1) + 3;
-
     huff_status e;
     if (c.autotune) {
         e = autotune(p);
     } else {
-        p->cur = Setting{c.reduce_log2, c.max_subtiles ? c.max_subtiles : 8, c.ctas_per_sm, 10};
+        p->cur = Setting{c.reduce_log2, c.max_subtiles ? c.max_subtiles : 8, c.ctas_per_sm, 10,
+                         c.per_field ? 16 : 0};
         e = apply_chunks(p, 10);
         if (e == HUFF_OK) e = capture(p, p->cur);
     }
@@ -426,6 +556,7 @@ huff_status huff_batch_plan_create(const huff_field *fields, uint32_t nfields, c
         free_plan(p);
         return e;
     }
+    p->kernels_per_run = count_kernels(p);
     *out = p;
     return HUFF_OK;
 }
@@ -482,6 +613,8 @@ huff_status huff_batch_get_info(const huff_batch_plan *p, huff_batch_info *info)
     info->candidates = p->candidates;
     info->tuned_ms = p->tuned_ms;
     info->device_bytes = p->dbytes;
+    info->per_field = p->cur.per_field ? 1u : 0u;
+    info->per_field_tiles = (uint32_t)p->cur.per_field;
     return HUFF_OK;
 }
 

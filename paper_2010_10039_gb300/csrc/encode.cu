@@ -31,6 +31,27 @@ __global__ void entry_table_kernel(const uint8_t *book, uint32_t nbins, uint32_t
         etab[i] = entry_from_cw<uint32_t>(gcw[i]);
 }
 
+uint32_t encode_kernels_per_call(uint32_t nbins) {
+    return 1u + (nbins > kEncSmemTableBins && nbins <= kEncEntryTableBins ? 1u : 0u);
+}
+
+template <typename Sym>
+static huff_status prepare_one(uint32_t nbins) {
+    const bool gtab = nbins > kEncSmemTableBins;
+    const void *k = (!gtab || nbins <= kEncEntryTableBins) ? (const void *)encode_one_kernel_get<Sym>(gtab)
+                                                            : (const void *)encode_kernel<Sym, true, false>;
+    return allow_dynamic_smem(k, 0) ? HUFF_OK : HUFF_ERR_CUDA;
+}
+
+huff_status encode_prepare(huff_dtype dtype, uint32_t nbins) {
+    switch (dtype) {
+        case HUFF_U8: return prepare_one<uint8_t>(nbins);
+        case HUFF_U16: return prepare_one<uint16_t>(nbins);
+        case HUFF_U32: return prepare_one<uint32_t>(nbins);
+    }
+    return HUFF_ERR_INVALID_ARG;
+}
+
 static uint32_t pow2_at_least(uint32_t x) {
     uint32_t p = 1;
     while (p < x) p <<= 1;
@@ -41,7 +62,8 @@ template <typename Sym>
 static huff_status launch_encode(const void *d_sym, uint64_t n, const void *d_codebook, uint32_t nbins_host,
                                  int chunk_log2, int reduce_log2, uint32_t format, uint32_t *d_out, uint64_t cap,
                                  uint64_t *d_offs, uint64_t *d_total, uint8_t *scratch, uint32_t *status,
-                                 cudaStream_t st, uint32_t id_offset, uint32_t spin_limit) {
+                                 cudaStream_t st, uint32_t id_offset, uint32_t spin_limit, bool zeroed,
+                                 uint32_t tiles_per_cta) {
     constexpr uint32_t SUB = enc_sub_syms<Sym>();
     EncArgs a{};
     a.one.sym = static_cast<const uint8_t *>(d_sym);
@@ -68,7 +90,7 @@ static huff_status launch_encode(const void *d_sym, uint64_t n, const void *d_co
     a.id_offset = id_offset;
     a.spin_limit = spin_limit;
     const uint64_t max_tiles = (n + SUB - 1) / SUB;
-    if (cudaMemsetAsync(scratch, 0, 64 + 16 * max_tiles, st) != cudaSuccess) return HUFF_ERR_CUDA;
+    if (!zeroed && cudaMemsetAsync(scratch, 0, 64 + 16 * max_tiles, st) != cudaSuccess) return HUFF_ERR_CUDA;
     const bool gtab = nbins_host > kEncSmemTableBins;
     if (gtab && nbins_host <= kEncEntryTableBins) {
         uint32_t *etab = reinterpret_cast<uint32_t *>(scratch + desc_area_bytes(n));
@@ -79,6 +101,10 @@ static huff_status launch_encode(const void *d_sym, uint64_t n, const void *d_co
     size_t smem = enc_smem_bytes<Sym>(gtab, a.tslots, 0);
     void (*kern)(EncArgs);
     int threads = kEncCtaThreads;
+    // tiles the grid is sized for: sub-tiles, or segment tiles where the
+    // segment path may run (the general encoder's tiles then hold up to 8
+    // sub-tiles, about a segment tile's symbols)
+    uint64_t tiles = max_tiles;
     if (fmt_chunk_aligned(format)) {
         kern = encode_kernel_aligned<Sym>(gtab);
     } else if (!gtab || a.etab) {
@@ -86,6 +112,7 @@ static huff_status launch_encode(const void *d_sym, uint64_t n, const void *d_co
         // else the general encoder: room for either layout
         kern = encode_one_kernel_get<Sym>(gtab);
         threads = kSegThreads;
+        tiles = (n + seg_sub_syms<Sym>() - 1) / seg_sub_syms<Sym>();
         const size_t seg = seg_smem_bytes<Sym>(a.tslots, gtab);
         if (seg > smem) smem = seg;
     } else {
@@ -97,7 +124,8 @@ static huff_status launch_encode(const void *d_sym, uint64_t n, const void *d_co
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
     if (occ < 1) occ = 1;
     uint64_t grid = (uint64_t)sm_count() * occ;
-    if (grid > max_tiles) grid = max_tiles;
+    const uint64_t per = tiles_per_cta > 1 ? tiles_per_cta : 1;
+    if (grid > (tiles + per - 1) / per) grid = (tiles + per - 1) / per;
     kern<<<(unsigned)grid, threads, smem, st>>>(a);
     note_launch();
     return cudaGetLastError() == cudaSuccess ? HUFF_OK : HUFF_ERR_CUDA;
@@ -106,11 +134,11 @@ static huff_status launch_encode(const void *d_sym, uint64_t n, const void *d_co
 huff_status encode_launch_ex(const void *d_sym, uint64_t n, huff_dtype dtype, const void *d_codebook, uint32_t nbins,
                              int chunk_log2, int reduce_log2, uint32_t format, uint32_t *d_out, uint64_t cap,
                              uint64_t *d_offs, uint64_t *d_total, uint8_t *scratch, uint32_t *status, cudaStream_t st,
-                             uint32_t id_offset, uint32_t spin_limit) {
+                             uint32_t id_offset, uint32_t spin_limit, bool zeroed, uint32_t tiles_per_cta) {
     switch (dtype) {
-        case HUFF_U8: return launch_encode<uint8_t>(d_sym, n, d_codebook, nbins, chunk_log2, reduce_log2, format, d_out, cap, d_offs, d_total, scratch, status, st, id_offset, spin_limit);
-        case HUFF_U16: return launch_encode<uint16_t>(d_sym, n, d_codebook, nbins, chunk_log2, reduce_log2, format, d_out, cap, d_offs, d_total, scratch, status, st, id_offset, spin_limit);
-        case HUFF_U32: return launch_encode<uint32_t>(d_sym, n, d_codebook, nbins, chunk_log2, reduce_log2, format, d_out, cap, d_offs, d_total, scratch, status, st, id_offset, spin_limit);
+        case HUFF_U8: return launch_encode<uint8_t>(d_sym, n, d_codebook, nbins, chunk_log2, reduce_log2, format, d_out, cap, d_offs, d_total, scratch, status, st, id_offset, spin_limit, zeroed, tiles_per_cta);
+        case HUFF_U16: return launch_encode<uint16_t>(d_sym, n, d_codebook, nbins, chunk_log2, reduce_log2, format, d_out, cap, d_offs, d_total, scratch, status, st, id_offset, spin_limit, zeroed, tiles_per_cta);
+        case HUFF_U32: return launch_encode<uint32_t>(d_sym, n, d_codebook, nbins, chunk_log2, reduce_log2, format, d_out, cap, d_offs, d_total, scratch, status, st, id_offset, spin_limit, zeroed, tiles_per_cta);
     }
     return HUFF_ERR_INVALID_ARG;
 }
@@ -119,7 +147,7 @@ huff_status encode_launch(const void *d_sym, uint64_t n, huff_dtype dtype, const
                           int chunk_log2, int reduce_log2, uint32_t format, uint32_t *d_out, uint64_t cap,
                           uint64_t *d_offs, uint64_t *d_total, uint8_t *scratch, uint32_t *status, cudaStream_t st) {
     return encode_launch_ex(d_sym, n, dtype, d_codebook, nbins, chunk_log2, reduce_log2, format, d_out, cap, d_offs,
-                            d_total, scratch, status, st, 0u, 0u);
+                            d_total, scratch, status, st, 0u, 0u, false, 1u);
 }
 
 huff_status encode_format_of(const huff_params &p, huff_dtype dtype, uint32_t *fmt) {

@@ -101,12 +101,21 @@ huff_status encode_launch(const void *d_sym, uint64_t n, huff_dtype dtype, const
 // The same with two failure-detection knobs: id_offset is added to every tile
 // id the encoder takes (1 leaves tile 0 unencoded, so the look-back of tile 1
 // can only give up), and spin_limit bounds the look-back's polls (0: the
-// default limit).
+// default limit).  scratch_zeroed: the caller has cleared the scratch (the
+// batched plan clears every field's with one memset).  min_tiles_per_cta: the
+// grid holds at most one CTA per that many tiles (concurrent launches of
+// many fields share the GPU; a CTA's start-up is paid once per CTA).
 huff_status encode_launch_ex(const void *d_sym, uint64_t n, huff_dtype dtype, const void *d_codebook, uint32_t nbins,
                              int chunk_log2, int reduce_log2, uint32_t format, uint32_t *d_out, uint64_t cap,
                              uint64_t *d_offs, uint64_t *d_total, uint8_t *scratch, uint32_t *status, cudaStream_t st,
-                             uint32_t id_offset, uint32_t spin_limit);
+                             uint32_t id_offset, uint32_t spin_limit, bool scratch_zeroed = false,
+                             uint32_t min_tiles_per_cta = 1);
 size_t encode_scratch_bytes(uint64_t n, uint32_t nbins);
+// Kernel launches of one encode_launch_ex call on a non-empty field.
+uint32_t encode_kernels_per_call(uint32_t nbins);
+// Sets the launch attributes encode_launch_ex needs for a dense field of this
+// dtype and alphabet size, so that later launches can be captured.
+huff_status encode_prepare(huff_dtype dtype, uint32_t nbins);
 int encode_run_log2(huff_dtype dtype);
 // Symbols per sub-tile (the smallest tile) of a dtype.
 uint32_t encode_sub_symbols(huff_dtype dtype);

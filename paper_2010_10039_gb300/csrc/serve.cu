@@ -74,6 +74,7 @@ struct Ctx {
     uint32_t *d_status = nullptr, *h_status = nullptr;
     uint64_t *d_total = nullptr, *h_total = nullptr;
     uint8_t *d_escr = nullptr, *d_cbscr = nullptr;
+    size_t escr_bytes = 0;
     size_t cbscr_stride = 0;
     uint64_t max_tiles = 0;
 };
@@ -283,6 +284,15 @@ huff_status launch_batch(huff_server *s, Ctx *c, const std::vector<Job *> &jb0, 
         e = codebook_batch_launch(c->d_cb + g.first, g.count, g.max_nbins, grid_c,
                                   g.max_nbins > 4096 ? c->d_cbscr : nullptr, c->cbscr_stride, st);
         if (e != HUFF_OK) return e;
+        const EncField &f1 = c->h_ef[g.first];
+        if (g.count == 1 && encode_scratch_bytes(f1.n, f1.nbins) <= c->escr_bytes) {
+            // a group of one job: the single-field encoder (its segment path
+            // where the job's codewords allow it)
+            e = encode_launch_ex(f1.sym, f1.n, g.dtype, f1.book, f1.nbins, f1.chunk_log2, -1, 0u, f1.out,
+                                 f1.cap_words, f1.offs, f1.total_bits, c->d_escr, f1.status, st, 0u, 0u);
+            if (e != HUFF_OK) return e;
+            continue;
+        }
         e = encode_batch_plan_launch(g.dtype, c->d_ef + g.first, g.count, c->d_conf + gi, -1, 8, st);
         if (e != HUFF_OK) return e;
         if (cudaMemsetAsync(c->d_escr, 0, 64 + 16 * g.enc_tiles, st) != cudaSuccess) return HUFF_ERR_CUDA;
@@ -472,6 +482,7 @@ huff_status huff_serve_create(const huff_serve_cfg *cfg, huff_server **out) {
         x.d_status = reinterpret_cast<uint32_t *>(x.dmem + o_status);
         x.d_total = reinterpret_cast<uint64_t *>(x.dmem + o_total);
         x.d_escr = x.dmem + o_escr;
+        x.escr_bytes = align256(64 + 16 * enc_tiles);
         x.d_cbscr = x.dmem + o_cbscr;
         x.h_tiles = reinterpret_cast<HistTile *>(x.hmem + h_tiles);
         x.h_hf = reinterpret_cast<HistField *>(x.hmem + h_hf);

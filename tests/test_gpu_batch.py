@@ -78,10 +78,12 @@ def _run_and_check(fields_np, nbins_list, **kw):
     return plan, fields
 
 
-def test_batch_u16_mixed_sizes_chunks_and_alignment():
+@pytest.mark.parametrize("per_field", [False, True])
+def test_batch_u16_mixed_sizes_chunks_and_alignment(per_field):
     """Fields of very different sizes (empty, one symbol, sub-tile and tile
     boundaries, up to 1.5 M symbols), mixed chunk sizes and two unaligned
-    inputs, all in one batch."""
+    inputs, all in one batch; with one persistent encode launch and with one
+    launch per field."""
     sizes = [0, 1, 7, 4095, 4096, 4097, 8191, 8193, 32768, 32769, 65536 * 3 + 5, 1 << 20, 1_500_001,
              12345, 100_000, 2, 16, 17, 250_000, 777_777]
     fields_np = [_field_input(j, n, 1024, 2) for j, n in enumerate(sizes)]
@@ -89,10 +91,13 @@ def test_batch_u16_mixed_sizes_chunks_and_alignment():
     offs = [0] * len(sizes)
     offs[3] = 1
     offs[11] = 3
-    _run_and_check(fields_np, [1024] * len(sizes), chunk_list=chunks, offsets_elems=offs)
+    plan, _ = _run_and_check(fields_np, [1024] * len(sizes), chunk_list=chunks, offsets_elems=offs,
+                             per_field=per_field)
+    assert plan.info()["per_field"] == int(per_field)
 
 
-def test_batch_dtypes_and_alphabet_classes():
+@pytest.mark.parametrize("per_field", [False, True])
+def test_batch_dtypes_and_alphabet_classes(per_field):
     """u8, u16 and u32 fields over small, medium (table in global memory) and
     large (packed histogram counters) alphabets in one plan: one launch group
     per dtype and alphabet class."""
@@ -107,7 +112,7 @@ def test_batch_dtypes_and_alphabet_classes():
                                     mapping=synth.permutation(3, K))); nbs.append(K)
     for j in range(2):
         fields_np.append(_field_input(30 + j, 123_457, 16384, 4, b=300.0)); nbs.append(16384)
-    plan, _ = _run_and_check(fields_np, nbs)
+    plan, _ = _run_and_check(fields_np, nbs, per_field=per_field)
     assert plan.info()["groups"] >= 4
 
 
@@ -132,7 +137,8 @@ def test_batch_settings_do_not_change_output(r, cap, ctas):
     _run_and_check(fields_np, [1024] * len(sizes), reduce_log2=r, max_subtiles=cap, ctas_per_sm=ctas)
 
 
-def test_batch_rerun_with_new_contents():
+@pytest.mark.parametrize("per_field", [False, True])
+def test_batch_rerun_with_new_contents(per_field):
     """The plan captures pointers: new data in the same buffers gives the new
     data's encoding on the next run."""
     import paper_2010_10039_gb300 as huff
@@ -141,7 +147,7 @@ def test_batch_rerun_with_new_contents():
     a1 = [_field_input(j, n, 1024, 2, seed=1) for j, n in enumerate(sizes)]
     a2 = [_field_input(j, n, 1024, 2, b=9.0, seed=2) for j, n in enumerate(sizes)]
     fields = _make(a1, [1024] * 3)
-    plan = huff.BatchPlan(fields)
+    plan = huff.BatchPlan(fields, per_field=per_field)
     plan.encode()
     torch.cuda.synchronize()
     for i in range(3):
@@ -156,7 +162,8 @@ def test_batch_rerun_with_new_contents():
         _check_field(plan, i, fields[i], a2[i], 1024)
 
 
-def test_batch_errors_stay_in_their_field():
+@pytest.mark.parametrize("per_field", [False, True])
+def test_batch_errors_stay_in_their_field(per_field):
     """A symbol beyond its field's alphabet and an output buffer that is too
     small each mark only their own field; the other fields are exact."""
     import paper_2010_10039_gb300 as huff
@@ -169,7 +176,7 @@ def test_batch_errors_stay_in_their_field():
     nbs = [1024, 900, 1024, 1024]
     fields = _make(fields_np, nbs)
     fields[2]["out"] = fields[2]["out"][:100]     # far too small
-    plan = huff.BatchPlan(fields)
+    plan = huff.BatchPlan(fields, per_field=per_field)
     plan.encode()
     torch.cuda.synchronize()
     st = plan.status()
@@ -189,14 +196,16 @@ def test_batch_more_than_one_group_of_fields():
     assert plan.info()["groups"] == 2
 
 
-def test_batch_launch_count_per_run():
+@pytest.mark.parametrize("per_field", [False, True])
+def test_batch_launch_count_per_run(per_field):
     import paper_2010_10039_gb300 as huff
     import torch
-    fields_np = [_field_input(j, 10_000, 1024, 2) for j in range(3)]
-    fields = _make(fields_np, [1024] * 3)
-    plan = huff.BatchPlan(fields)
+    fields_np = [_field_input(j, 10_000, 1024, 2) for j in range(3)] + [np.zeros(0, np.uint16)]
+    fields = _make(fields_np, [1024] * 4)
+    plan = huff.BatchPlan(fields, per_field=per_field)
     k = plan.info()["kernels_per_run"]
-    assert k == 4
+    # histogram and codebooks, then the tile planner and one encode, or one encode per non-empty field
+    assert k == (5 if per_field else 4)
     c0 = huff.huff_launch_count()
     plan.encode()
     torch.cuda.synchronize()
