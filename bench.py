@@ -772,7 +772,7 @@ def run_batched(args, world, rank, local):
                 "total_bits": torch.zeros_like(f["total_bits"])} for f in fields]
     plan2 = huff.BatchPlan(fields2, autotune=False, reduce_log2=info["reduce_log2"],
                            max_subtiles=info["max_subtiles"], ctas_per_sm=info["ctas_per_sm"],
-                           per_field=bool(info["per_field"]))
+                           encode_form=info["encode_form"])
     sets = [(fields, plan), (fields2, plan2)]
     host_out = [[torch.empty(max(1, w), dtype=torch.int32).pin_memory() for w in nw] for _ in range(2)]
     host_off = [[torch.empty_like(f["offsets"], device="cpu").pin_memory() for f in fields] for _ in range(2)]
@@ -850,8 +850,10 @@ def run_batched(args, world, rank, local):
         "plan": {k: (round(v, 4) if isinstance(v, float) else v) for k, v in info.items()},
         "plan_create_s": round(t_plan, 3),
         "stages_ms_ungraphed": {k: round(v, 4) for k, v in stages.items()},
-        "roofline": {"bound": "hbm", "kernel": ("batched encode (one single-field launch per field, concurrent)"
-                                                if info["per_field"] else "batched encode (one launch, all fields)"),
+        "roofline": {"bound": "hbm", "kernel": {0: "batched encode (one launch, all fields)",
+                                                1: "batched encode (one single-field launch per field, concurrent)",
+                                                2: "batched encode (segment encoder over the fields it takes, then "
+                                                   "the general encoder over the rest)"}[info["encode_form"]],
                      "achieved": round(enc_alg / (enc_ms * 1e-3) / 1e9, 2), "peak": peak, "peak_kind": peak_kind,
                      "unit": "GB/s", "frac": round(enc_alg / (enc_ms * 1e-3) / 1e9 / peak, 4), "traffic": None,
                      "algorithmic_bytes": enc_alg},

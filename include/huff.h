@@ -330,11 +330,14 @@ typedef struct {
                                length (used when not tuning)                                            */
     int32_t max_subtiles;   /* sub-tiles per encode tile, 1..8; 0 = 8 (used when not tuning)             */
     int32_t ctas_per_sm;    /* encode CTAs per SM; 0 = as many as fit (used when not tuning)            */
-    int32_t per_field;      /* 0: the encode stage is one persistent launch over all fields of a group;
+    int32_t encode_form;    /* 0: the encode stage is one persistent launch of the general encoder over
+                               all fields of a group;
                                1: one single-field encode launch per field (as huff_encode: the segment
                                encoder where a field's codewords allow it), run concurrently on the
-                               plan's side streams inside the graph; r as above, the sub-tile and CTA
-                               settings then unused (used when not tuning; the tuner times both)      */
+                               plan's side streams inside the graph;
+                               2: one persistent launch of the segment encoder over the fields whose
+                               codewords fit it (at most 23 bits), then the general encoder over the
+                               rest (used when not tuning; the tuner times all three)                */
 } huff_batch_cfg;
 
 typedef struct {
@@ -347,7 +350,7 @@ typedef struct {
     uint32_t candidates;     /* settings timed by the tuner (0: not tuned)                        */
     float tuned_ms;          /* best time of one batch during tuning                              */
     uint64_t device_bytes;   /* device memory held by the plan                                    */
-    uint32_t per_field;      /* encode form in use (huff_batch_cfg.per_field)                     */
+    uint32_t encode_form;    /* encode form in use (huff_batch_cfg.encode_form)                   */
     uint32_t per_field_tiles;/* per-field form: least tiles per CTA of each launch (0: not in use)  */
 } huff_batch_info;
 

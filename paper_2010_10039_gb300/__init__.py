@@ -55,14 +55,14 @@ class huff_field(ctypes.Structure):
 class huff_batch_cfg(ctypes.Structure):
     _fields_ = [("autotune", ctypes.c_int32), ("reduce_log2", ctypes.c_int32),
                 ("max_subtiles", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("per_field", ctypes.c_int32)]
+                ("encode_form", ctypes.c_int32)]
 
 
 class huff_batch_info(ctypes.Structure):
     _fields_ = [("reduce_log2", ctypes.c_int32), ("max_subtiles", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("chunk_log2", ctypes.c_int32), ("groups", ctypes.c_uint32), ("kernels_per_run", ctypes.c_uint32),
                 ("candidates", ctypes.c_uint32), ("tuned_ms", ctypes.c_float), ("device_bytes", ctypes.c_uint64),
-                ("per_field", ctypes.c_uint32), ("per_field_tiles", ctypes.c_uint32)]
+                ("encode_form", ctypes.c_uint32), ("per_field_tiles", ctypes.c_uint32)]
 
 
 class huff_serve_cfg(ctypes.Structure):
@@ -375,7 +375,7 @@ class BatchPlan:
     choose).  The tensors must outlive the plan."""
 
     def __init__(self, fields, autotune: bool = False, reduce_log2: int = -1, max_subtiles: int = 0,
-                 ctas_per_sm: int = 0, per_field: bool = False, stream=None):
+                 ctas_per_sm: int = 0, encode_form: int = 0, stream=None):
         self._keep = fields
         self.n = len(fields)
         arr = (huff_field * self.n)()
@@ -396,7 +396,7 @@ class BatchPlan:
         cfg.reduce_log2 = reduce_log2
         cfg.max_subtiles = max_subtiles
         cfg.ctas_per_sm = ctas_per_sm
-        cfg.per_field = 1 if per_field else 0
+        cfg.encode_form = encode_form
         h = ctypes.c_void_p()
         _check(lib().huff_batch_plan_create(arr, self.n, ctypes.byref(cfg), _stream(stream), ctypes.byref(h)),
                "huff_batch_plan_create")

@@ -2,10 +2,12 @@
 // layout, capture of the launch set in a CUDA graph, and the autotuner that
 // picks the encoder's reduction factor, tile size, CTAs per SM and (for
 // fields that leave it open) chunk size by timing the graph on the fields.
-// The encode stage takes one of two forms: one persistent launch whose tiles
-// run over all fields of a group, or one single-field launch per field (the
-// segment encoder wherever the field's codewords allow it), fanned out over
-// side streams inside the graph; the tuner times both.
+// The encode stage takes one of three forms: one persistent launch of the
+// general encoder whose tiles run over all fields of a group; one
+// single-field launch per field (the segment encoder wherever the field's
+// codewords allow it), fanned out over side streams inside the graph; or one
+// persistent launch of the segment encoder over the fields whose codewords
+// fit it, then the general encoder over the rest.  The tuner times all three.
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -44,6 +46,8 @@ struct BatchGroup {
     int enc_occ = 1;                    // encode CTAs per SM that fit
     size_t off_fscr = 0, fscr_bytes = 0;
     std::vector<size_t> fscr;           // per field: its single-field encode scratch, from off_fscr
+    size_t off_sfirst = 0, off_sscr = 0, sscr_bytes = 0, off_etab = 0;   // batched segment form
+    bool seg_many = false;              // some field's chunks are shorter than a segment
     std::vector<uint32_t> by_size;      // field positions, most symbols first
 };
 
@@ -53,6 +57,7 @@ struct Setting {
     int ctas_per_sm;    // 0 = as many as fit
     int chunk_log2;     // M for fields created with -1
     int per_field;      // k >= 1: one single-field encode launch per field, at least k tiles per CTA
+    int seg;            // 1: the batched segment form (per_field 0)
 };
 
 }  // namespace huff
@@ -108,11 +113,13 @@ huff_status apply_chunks(huff_batch_plan *p, int auto_m) {
     for (uint32_t i = 0; i < p->fields.size(); i++)
         p->chunk_log2[i] = p->auto_chunk[i] ? auto_m : p->fields[i].chunk_log2;
     for (BatchGroup &g : p->groups) {
+        g.seg_many = false;
         for (size_t k = 0; k < g.idx.size(); k++) {
             EncField &e = g.efields[k];
             const int m = p->chunk_log2[g.idx[k]];
             e.chunk_log2 = m;
             e.nchunks = (e.n + (1ull << m) - 1) >> m;
+            if ((1ull << m) < encode_seg_lane_symbols(g.dtype)) g.seg_many = true;
         }
         if (cudaMemcpyAsync(p->dmem + g.off_ef, g.efields.data(), g.efields.size() * sizeof(EncField),
                             cudaMemcpyHostToDevice, p->cs) != cudaSuccess)
@@ -148,7 +155,7 @@ huff_status encode_fields(huff_batch_plan *p, const BatchGroup &g, const Setting
                                                p->chunk_log2[i], s.r, 0u, static_cast<uint32_t *>(f.d_out),
                                                f.out_capacity_words, f.d_chunk_bit_offset, f.d_total_bits,
                                                p->dmem + g.off_fscr + g.fscr[fi], status_ptr(p, i), p->side[k], 0u,
-                                               0u, true, (uint32_t)s.per_field);
+                                               0u, true, (uint32_t)s.per_field, true);
         if (e != HUFF_OK) return e;
     }
     for (int k = 0; k < ns; k++) {
@@ -182,6 +189,28 @@ huff_status record(huff_batch_plan *p, const Setting &s, cudaStream_t st, const 
         e = codebook_batch_launch(reinterpret_cast<const CbArgs *>(p->dmem + g.off_cb), nf, g.max_nbins, g.grid_c,
                                   g.cbscr_stride ? p->dmem + g.off_cbscr : nullptr, g.cbscr_stride, st);
         if (e != HUFF_OK) return e;
+        if (s.seg) {
+            EncField *ef = reinterpret_cast<EncField *>(p->dmem + g.off_ef);
+            EncBatchConf *conf = reinterpret_cast<EncBatchConf *>(p->dmem + g.off_conf);
+            uint32_t *sfirst = reinterpret_cast<uint32_t *>(p->dmem + g.off_sfirst);
+            if (!mark(2)) return HUFF_ERR_CUDA;
+            e = encode_batch_plan_launch(g.dtype, ef, nf, conf, s.r, (uint32_t)s.max_subtiles, st, sfirst);
+            if (e != HUFF_OK) return e;
+            if (cudaMemsetAsync(p->dmem + g.off_escr, 0, g.escr_bytes, st) != cudaSuccess ||
+                cudaMemsetAsync(p->dmem + g.off_sscr, 0, g.sscr_bytes, st) != cudaSuccess)
+                return HUFF_ERR_CUDA;
+            if (!mark(3)) return HUFF_ERR_CUDA;
+            e = encode_seg_batch_launch(g.dtype, ef, nf, conf, sfirst, g.max_nbins, p->dmem + g.off_sscr,
+                                        (uint32_t)(sms * 2), g.seg_many, st);
+            if (e != HUFF_OK) return e;
+            int c = s.ctas_per_sm <= 0 ? g.enc_occ : std::min(s.ctas_per_sm, g.enc_occ);
+            if (c < 1) c = 1;
+            e = encode_batch_launch(g.dtype, ef, nf, conf, g.max_nbins, p->dmem + g.off_escr, (uint32_t)(sms * c), st);
+            if (e != HUFF_OK) return e;
+            if (!mark(4)) return HUFF_ERR_CUDA;
+            gi++;
+            continue;
+        }
         if (s.per_field) {
             if (!mark(2)) return HUFF_ERR_CUDA;
             if (cudaMemsetAsync(p->dmem + g.off_fscr, 0, g.fscr_bytes, st) != cudaSuccess) return HUFF_ERR_CUDA;
@@ -213,6 +242,10 @@ uint32_t count_kernels(const huff_batch_plan *p) {
     uint32_t k = 0;
     for (const BatchGroup &g : p->groups) {
         k += (g.tiles.empty() ? 0 : 1) + 1;                 // histogram, codebooks
+        if (p->cur.seg) {
+            k += 4;                                          // planner, entry tables, both encoders
+            continue;
+        }
         if (!p->cur.per_field) {
             k += 2;                                          // tile planner, encode
             continue;
@@ -289,7 +322,7 @@ huff_status autotune(huff_batch_plan *p) {
     }
     const bool any_auto = std::find(p->auto_chunk.begin(), p->auto_chunk.end(), 1) != p->auto_chunk.end();
     std::vector<int> ms_list = any_auto ? std::vector<int>(kAutoChunkLog2, kAutoChunkLog2 + 3) : std::vector<int>{0};
-    Setting best{-1, 8, 0, any_auto ? 10 : 0, 0};
+    Setting best{-1, 8, 0, any_auto ? 10 : 0, 0, 0};
     float best_ms = 1e30f;
     uint32_t count = 0;
     huff_status e0 = apply_chunks(p, 10);
@@ -297,7 +330,7 @@ huff_status autotune(huff_batch_plan *p) {
     for (int r = rmin; r <= rmax; r++)
         for (int cap : {2, 4, 8})
             for (int c = 1; c <= std::min(occ, 3); c++) {
-                Setting s{r, cap, c, 0, 0};
+                Setting s{r, cap, c, 0, 0, 0};
                 huff_status e = capture(p, s);
                 if (e != HUFF_OK) return e;
                 for (int m : ms_list) {
@@ -313,8 +346,11 @@ huff_status autotune(huff_batch_plan *p) {
                 }
             }
     // one launch per field (r by rule: on the segment path r moves the time little)
-    for (int per : kPerFieldTiles) {
-        const Setting s{-1, 8, 0, 0, per};
+    // the batched segment form (r by rule over its fields; the rest keeps the
+    // general encoder at 8 sub-tiles and the CTAs that fit), then one launch
+    // per field
+    for (int per : {0, kPerFieldTiles[0], kPerFieldTiles[1], kPerFieldTiles[2]}) {
+        const Setting s{-1, 8, 0, 0, per, per == 0 ? 1 : 0};
         huff_status e = capture(p, s);
         if (e != HUFF_OK) return e;
         for (int m : ms_list) {
@@ -365,7 +401,7 @@ void huff_batch_default_cfg(huff_batch_cfg *cfg) {
     cfg->reduce_log2 = -1;
     cfg->max_subtiles = 0;
     cfg->ctas_per_sm = 0;
-    cfg->per_field = 0;
+    cfg->encode_form = 0;
 }
 
 huff_status huff_batch_plan_create(const huff_field *fields, uint32_t nfields, const huff_batch_cfg *cfg,
@@ -377,7 +413,7 @@ huff_status huff_batch_plan_create(const huff_field *fields, uint32_t nfields, c
     huff_batch_default_cfg(&c);
     if (cfg) c = *cfg;
     if (c.reduce_log2 < -1 || c.reduce_log2 > 4 || c.max_subtiles < 0 || c.max_subtiles > 8 || c.ctas_per_sm < 0 ||
-        (c.per_field != 0 && c.per_field != 1))
+        c.encode_form < 0 || c.encode_form > 2)
         return HUFF_ERR_INVALID_ARG;
     for (uint32_t i = 0; i < nfields; i++)
         if (!field_ok(fields[i])) return HUFF_ERR_INVALID_ARG;
@@ -449,6 +485,16 @@ huff_status huff_batch_plan_create(const huff_field *fields, uint32_t nfields, c
         }
         g.fscr_bytes = std::max<size_t>(fs, 256);
         g.off_fscr = take(g.fscr_bytes);
+        // batched segment form: first tile ids, descriptors, entry tables
+        uint64_t seg_tiles = 0;
+        const uint32_t seg_sub = encode_seg_tile_symbols(g.dtype);
+        for (uint32_t i : g.idx) seg_tiles += (fields[i].n + seg_sub - 1) / seg_sub;
+        g.off_sfirst = take(4ull * (g.idx.size() + 1));
+        g.sscr_bytes = 64 + 16 * seg_tiles;
+        g.off_sscr = take(g.sscr_bytes);
+        size_t et = 0;
+        for (uint32_t i : g.idx) et += align_up(4ull * fields[i].nbins, 16);
+        g.off_etab = take(std::max<size_t>(et, 16));
         g.by_size.resize(g.idx.size());
         for (uint32_t fi = 0; fi < g.idx.size(); fi++) g.by_size[fi] = fi;
         std::stable_sort(g.by_size.begin(), g.by_size.end(),
@@ -458,6 +504,7 @@ huff_status huff_batch_plan_create(const huff_field *fields, uint32_t nfields, c
         huff_status e = histogram_batch_prepare(g.dtype, g.max_nbins, &occ_h);
         if (e == HUFF_OK) e = codebook_batch_prepare(g.max_nbins, &occ_c);
         if (e == HUFF_OK) e = encode_batch_prepare(g.dtype, g.max_nbins, (uint32_t)g.idx.size(), &g.enc_occ);
+        if (e == HUFF_OK) e = encode_seg_batch_prepare(g.dtype, (uint32_t)g.idx.size());
         for (uint32_t fi = 0; fi < g.idx.size() && e == HUFF_OK; fi++)
             e = encode_prepare(g.dtype, fields[g.idx[fi]].nbins);
         if (e != HUFF_OK) {
@@ -505,6 +552,7 @@ huff_status huff_batch_plan_create(const huff_field *fields, uint32_t nfields, c
 
     // ---- records
     for (BatchGroup &g : p->groups) {
+        size_t et = 0;
         for (uint32_t fi = 0; fi < g.idx.size(); fi++) {
             const uint32_t i = g.idx[fi];
             const huff_field &f = fields[i];
@@ -525,6 +573,8 @@ huff_status huff_batch_plan_create(const huff_field *fields, uint32_t nfields, c
             e.cap_words = f.out_capacity_words;
             e.nbins = f.nbins;
             e.aligned = ((uintptr_t)f.d_sym & 15) == 0;
+            e.etab = reinterpret_cast<uint32_t *>(p->dmem + g.off_etab + et);
+            et += align_up(4ull * f.nbins, 16);
             g.efields.push_back(e);
         }
         cudaError_t ce = cudaSuccess;
@@ -547,7 +597,7 @@ huff_status huff_batch_plan_create(const huff_field *fields, uint32_t nfields, c
         e = autotune(p);
     } else {
         p->cur = Setting{c.reduce_log2, c.max_subtiles ? c.max_subtiles : 8, c.ctas_per_sm, 10,
-                         c.per_field ? 16 : 0};
+                         c.encode_form == 1 ? 16 : 0, c.encode_form == 2 ? 1 : 0};
         e = apply_chunks(p, 10);
         if (e == HUFF_OK) e = capture(p, p->cur);
     }
@@ -613,7 +663,7 @@ huff_status huff_batch_get_info(const huff_batch_plan *p, huff_batch_info *info)
     info->candidates = p->candidates;
     info->tuned_ms = p->tuned_ms;
     info->device_bytes = p->dbytes;
-    info->per_field = p->cur.per_field ? 1u : 0u;
+    info->encode_form = p->cur.seg ? 2u : p->cur.per_field ? 1u : 0u;
     info->per_field_tiles = (uint32_t)p->cur.per_field;
     return HUFF_OK;
 }

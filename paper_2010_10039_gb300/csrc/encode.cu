@@ -16,19 +16,18 @@ size_t encode_scratch_bytes(uint64_t n, uint32_t nbins) {
     return desc_area_bytes(n) + (nbins > kEncSmemTableBins ? 4ull * nbins : 0);
 }
 
-// The codebook's 32-bit table entries (code << (32 - l) | l), precomputed once
-// per launch when the codebook stays in global memory: a lookup then reads one
-// word instead of converting a 64-bit codeword, and the segment path, which
-// takes only 32-bit entries, can run.  Codes over 23 bits keep the 64-bit
-// codewords (the encoder then ignores this table).  Up to 65,536 entries (the
-// allocation-free entry point's array holds that many).
+// The codebook's 32-bit table entries (code << (32 - l) | l, a flag entry for
+// codewords over 23 bits), precomputed once per launch when the codebook stays
+// in global memory: a lookup then reads one word instead of converting a
+// 64-bit codeword, and the segment path, which takes 32-bit entries, can run.
+// The general encoder reads them only when every codeword has at most 23
+// bits.  Up to 65,536 entries (the allocation-free entry point's array holds
+// that many).
 constexpr uint32_t kEncEntryTableBins = 65536;
 __global__ void entry_table_kernel(const uint8_t *book, uint32_t nbins, uint32_t *etab) {
-    const huff_codebook_header *hdr = reinterpret_cast<const huff_codebook_header *>(book);
-    if (hdr->max_len > 23) return;
     const uint64_t *gcw = reinterpret_cast<const uint64_t *>(book + cb_cw_offset());
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nbins; i += gridDim.x * blockDim.x)
-        etab[i] = entry_from_cw<uint32_t>(gcw[i]);
+        etab[i] = seg_entry_from_cw(gcw[i]);
 }
 
 uint32_t encode_kernels_per_call(uint32_t nbins) {
@@ -38,7 +37,7 @@ uint32_t encode_kernels_per_call(uint32_t nbins) {
 template <typename Sym>
 static huff_status prepare_one(uint32_t nbins) {
     const bool gtab = nbins > kEncSmemTableBins;
-    const void *k = (!gtab || nbins <= kEncEntryTableBins) ? (const void *)encode_one_kernel_get<Sym>(gtab)
+    const void *k = (!gtab || nbins <= kEncEntryTableBins) ? (const void *)encode_one_kernel_get<Sym>(gtab, true)
                                                             : (const void *)encode_kernel<Sym, true, false>;
     return allow_dynamic_smem(k, 0) ? HUFF_OK : HUFF_ERR_CUDA;
 }
@@ -63,7 +62,7 @@ static huff_status launch_encode(const void *d_sym, uint64_t n, const void *d_co
                                  int chunk_log2, int reduce_log2, uint32_t format, uint32_t *d_out, uint64_t cap,
                                  uint64_t *d_offs, uint64_t *d_total, uint8_t *scratch, uint32_t *status,
                                  cudaStream_t st, uint32_t id_offset, uint32_t spin_limit, bool zeroed,
-                                 uint32_t tiles_per_cta) {
+                                 uint32_t tiles_per_cta, bool long_ok) {
     constexpr uint32_t SUB = enc_sub_syms<Sym>();
     EncArgs a{};
     a.one.sym = static_cast<const uint8_t *>(d_sym);
@@ -110,7 +109,7 @@ static huff_status launch_encode(const void *d_sym, uint64_t n, const void *d_co
     } else if (!gtab || a.etab) {
         // the segment path when the codebook allows it (decided on the device),
         // else the general encoder: room for either layout
-        kern = encode_one_kernel_get<Sym>(gtab);
+        kern = encode_one_kernel_get<Sym>(gtab, long_ok);
         threads = kSegThreads;
         tiles = (n + seg_sub_syms<Sym>() - 1) / seg_sub_syms<Sym>();
         const size_t seg = seg_smem_bytes<Sym>(a.tslots, gtab);
@@ -134,11 +133,12 @@ static huff_status launch_encode(const void *d_sym, uint64_t n, const void *d_co
 huff_status encode_launch_ex(const void *d_sym, uint64_t n, huff_dtype dtype, const void *d_codebook, uint32_t nbins,
                              int chunk_log2, int reduce_log2, uint32_t format, uint32_t *d_out, uint64_t cap,
                              uint64_t *d_offs, uint64_t *d_total, uint8_t *scratch, uint32_t *status, cudaStream_t st,
-                             uint32_t id_offset, uint32_t spin_limit, bool zeroed, uint32_t tiles_per_cta) {
+                             uint32_t id_offset, uint32_t spin_limit, bool zeroed, uint32_t tiles_per_cta,
+                             bool long_ok) {
     switch (dtype) {
-        case HUFF_U8: return launch_encode<uint8_t>(d_sym, n, d_codebook, nbins, chunk_log2, reduce_log2, format, d_out, cap, d_offs, d_total, scratch, status, st, id_offset, spin_limit, zeroed, tiles_per_cta);
-        case HUFF_U16: return launch_encode<uint16_t>(d_sym, n, d_codebook, nbins, chunk_log2, reduce_log2, format, d_out, cap, d_offs, d_total, scratch, status, st, id_offset, spin_limit, zeroed, tiles_per_cta);
-        case HUFF_U32: return launch_encode<uint32_t>(d_sym, n, d_codebook, nbins, chunk_log2, reduce_log2, format, d_out, cap, d_offs, d_total, scratch, status, st, id_offset, spin_limit, zeroed, tiles_per_cta);
+        case HUFF_U8: return launch_encode<uint8_t>(d_sym, n, d_codebook, nbins, chunk_log2, reduce_log2, format, d_out, cap, d_offs, d_total, scratch, status, st, id_offset, spin_limit, zeroed, tiles_per_cta, long_ok);
+        case HUFF_U16: return launch_encode<uint16_t>(d_sym, n, d_codebook, nbins, chunk_log2, reduce_log2, format, d_out, cap, d_offs, d_total, scratch, status, st, id_offset, spin_limit, zeroed, tiles_per_cta, long_ok);
+        case HUFF_U32: return launch_encode<uint32_t>(d_sym, n, d_codebook, nbins, chunk_log2, reduce_log2, format, d_out, cap, d_offs, d_total, scratch, status, st, id_offset, spin_limit, zeroed, tiles_per_cta, long_ok);
     }
     return HUFF_ERR_INVALID_ARG;
 }
@@ -147,7 +147,7 @@ huff_status encode_launch(const void *d_sym, uint64_t n, huff_dtype dtype, const
                           int chunk_log2, int reduce_log2, uint32_t format, uint32_t *d_out, uint64_t cap,
                           uint64_t *d_offs, uint64_t *d_total, uint8_t *scratch, uint32_t *status, cudaStream_t st) {
     return encode_launch_ex(d_sym, n, dtype, d_codebook, nbins, chunk_log2, reduce_log2, format, d_out, cap, d_offs,
-                            d_total, scratch, status, st, 0u, 0u, false, 1u);
+                            d_total, scratch, status, st, 0u, 0u, false, 1u, false);
 }
 
 huff_status encode_format_of(const huff_params &p, huff_dtype dtype, uint32_t *fmt) {

@@ -69,6 +69,9 @@ struct EncArgs {
     uint32_t id_offset;           // added to every tile id taken (0; the failure-detection test
                                   // passes 1, so tile 0 is never encoded)
     uint32_t spin_limit;          // look-back polls before giving up (0: kSpinLimit)
+    const uint32_t *seg_first;    // batched segment form: first segment tile of every field, and the
+                                  // total after the last (nfields + 1 entries, from the planner)
+    uint32_t seg_many;            // batched segment form: some field has chunks shorter than a segment
 };
 
 // Tile id taken from the launch's counter.

@@ -6,10 +6,11 @@
 namespace huff {
 
 template <typename Sym>
-EncOneFn encode_one_kernel_get(bool gtab) {
-    return gtab ? encode_one_kernel<Sym, true> : encode_one_kernel<Sym, false>;
+EncOneFn encode_one_kernel_get(bool gtab, bool long_ok) {
+    if (long_ok) return gtab ? encode_one_kernel<Sym, true, true> : encode_one_kernel<Sym, false, true>;
+    return gtab ? encode_one_kernel<Sym, true, false> : encode_one_kernel<Sym, false, false>;
 }
 
-template EncOneFn encode_one_kernel_get<uint16_t>(bool);
+template EncOneFn encode_one_kernel_get<uint16_t>(bool, bool);
 
 }  // namespace huff

@@ -1,6 +1,8 @@
 // Segment encoder: Sec. IV-C reduce-merge and the placement that replaces the
-// shuffle-merge steps, for single-field launches whose codewords fit the
-// 32-bit table entry (at most 23 bits).
+// shuffle-merge steps.  Codewords of at most 23 bits fit the 32-bit table
+// entry; a longer one (rare: the field's least frequent symbols) has a flag
+// entry, and a segment that meets one takes its runs from the codebook's
+// 64-bit codewords instead.
 //
 // Every merge thread owns one contiguous segment of each tile: NV consecutive
 // 16-byte vectors of the staged tile (NV odd, so the 16-byte loads of eight
@@ -23,9 +25,9 @@
 // step for its stream offset, then the copy of its words from the ring into
 // the dense stream.
 //
-// Fields this path does not take (longer codewords, a chunk-aligned layout, a
-// tile that could outgrow the ring) run the general encoder in the same
-// launch; the choice is made on the device from the codebook header.
+// Fields this path does not take (a chunk-aligned layout, a tile that could
+// outgrow the ring) run the general encoder in the same launch; the choice is
+// made on the device from the codebook header.
 #pragma once
 
 #include "encode_impl.cuh"
@@ -70,7 +72,9 @@ struct SegGeom<uint32_t> {
 #define HUFF_SEG_SLOTS 8
 #endif
 constexpr int kSegSlots = HUFF_SEG_SLOTS;  // tiles between merge and write-out
-constexpr uint32_t kSegMaxLen = 23;        // longest codeword of the 32-bit table entry
+constexpr uint32_t kSegEntryLen = 23;      // longest codeword of the 32-bit table entry
+constexpr uint32_t kLong32 = 1u << 6;      // table entry of a longer codeword (bits 5..8 of an entry are free)
+constexpr uint32_t kSegMaxLen = kEncMaxLen;   // the ring's worst-case tile bounds it further
 constexpr uint32_t kSegRingPad = 32;       // words after the ring: the copy reads one word past a tile
 constexpr int kSegMaxStages = 4;
 #ifndef HUFF_SEG_HELPERS
@@ -111,8 +115,8 @@ __host__ __device__ inline bool seg_coff_smem(int chunk_log2) {
     return (seg_sub_syms<Sym>() >> chunk_log2) + 1 <= (uint32_t)kSegCoff;
 }
 
-// The path takes a codebook whose codewords fit the 32-bit entry and whose
-// worst-case tile (every codeword max_len bits) fits the ring.
+// The path takes a codebook whose worst-case tile (every codeword max_len
+// bits) fits the ring: up to 27 bits for u16 symbols, 42 for u8, 48 for u32.
 template <typename Sym>
 __host__ __device__ inline bool seg_fits(uint32_t max_len) {
     return max_len >= 1 && max_len <= kSegMaxLen &&
@@ -134,7 +138,15 @@ struct SegShared {
     uint32_t wtail[2][kEncThreads / 32]; // the warps' last 32 bits
     uint32_t coff[kSegSlots][kSegCoff];  // chunk offsets relative to the tile
     EncField f0;
+    uint32_t stage_field[kSegMaxStages]; // batched form: the field of each stage's tile
 };
+
+// The segment path's table entry of a codeword: the 32-bit entry up to 23
+// bits, kLong32 above, kBad32 for none.
+__device__ __forceinline__ uint32_t seg_entry_from_cw(uint64_t c) {
+    const uint32_t l = (uint32_t)(c >> HUFF_CW_LEN_SHIFT);
+    return l > kSegEntryLen ? kLong32 : entry_from_cw<uint32_t>(c);
+}
 
 // Shared-memory accesses by 32-bit shared-window address.  The table is
 // read-only once loaded, so its loads may be scheduled freely; stage loads
@@ -183,18 +195,26 @@ struct SegPut {
 
 // A run longer than 64 bits (rare: 2^r codewords of above 64 / 2^r bits on
 // average), codeword by codeword; symbols from global memory, since the stage
-// may be refilled already.  Out of line, so the common path keeps its
-// registers.
+// may be refilled already; flagged entries take the 64-bit codeword.  Out of
+// line, so the common path keeps its registers.
 template <typename Sym, int TAB>
 __device__ __noinline__ SegPut seg_put_long(SegPut st, const Sym *symp, uint64_t first, int count, uint64_t n,
-                                            const uint32_t *gtab, uint32_t tab_s, uint32_t nbins, uint32_t tmask) {
+                                            const uint32_t *gtab, uint32_t tab_s, uint32_t nbins, uint32_t tmask,
+                                            const uint64_t *gcw) {
     for (int x = 0; x < count; x++) {
         const uint64_t i = first + x;
         if (i >= n) break;
         const uint32_t sy = (uint32_t)symp[i];
         const uint32_t en = TAB == 2 ? (sy < nbins ? __ldg(gtab + sy) : kBad32) : lds_tab(tab_s + ((sy & tmask) << 2));
-        const uint32_t l = en & 31u;
-        seg_put(st.cur, st.e5, st.wa, 0u, l ? en >> (32u - l) : 0u, l);
+        if ((en & kLong32) && sy < nbins) {            // (a symbol out of range is an error already)
+            const uint64_t cw = gcw[sy];
+            const uint32_t l = (uint32_t)(cw >> HUFF_CW_LEN_SHIFT);
+            const uint64_t code = cw & ((1ull << l) - 1);
+            seg_put(st.cur, st.e5, st.wa, (uint32_t)(code >> 32), (uint32_t)code, l);
+        } else {
+            const uint32_t l = en & 31u;
+            seg_put(st.cur, st.e5, st.wa, 0u, l ? en >> (32u - l) : 0u, l);
+        }
     }
     return st;
 }
@@ -242,9 +262,21 @@ struct SegProducer {
     uint32_t slot;
 };
 
-template <typename Sym>
+// Batched form: the field of segment tile g, from the first tile ids
+// (sfirst[0] = 0 <= g < sfirst[nf]; fields without tiles are passed over).
+__device__ __forceinline__ uint32_t seg_field_of(const uint32_t *sfirst, uint32_t nf, uint32_t g) {
+    uint32_t lo = 0, hi = nf;              // sfirst[lo] <= g < sfirst[hi]
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (sfirst[mid] <= g) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <typename Sym, bool BATCH>
 __device__ __forceinline__ void seg_produce(const EncArgs &a, SegProducer &p, uint32_t total, uint8_t *stage,
-                                            SegShared &T) {
+                                            SegShared &T, const uint32_t *sfirst) {
     constexpr uint32_t SUB = seg_sub_syms<Sym>();
     constexpr uint32_t SUBB = seg_sub_bytes<Sym>();
     constexpr int NST = SegGeom<Sym>::NST;
@@ -256,10 +288,22 @@ __device__ __forceinline__ void seg_produce(const EncArgs &a, SegProducer &p, ui
     const int s = (int)(p.slot % NST);
     reinterpret_cast<volatile uint32_t *>(T.stage_tile)[s] = g;
     if (g < total) {
-        const uint64_t s0 = (uint64_t)g * SUB;
-        if (a.one.aligned && s0 + SUB <= a.one.n) {
+        const uint8_t *sym = a.one.sym;
+        uint64_t n = a.one.n, j = g;
+        bool aligned = a.one.aligned;
+        if constexpr (BATCH) {
+            const uint32_t f = seg_field_of(sfirst, a.nfields, g);
+            reinterpret_cast<volatile uint32_t *>(T.stage_field)[s] = f;
+            const EncField &F = a.fields[f];
+            sym = F.sym;
+            n = F.n;
+            aligned = F.aligned;
+            j = g - sfirst[f];
+        }
+        const uint64_t s0 = j * SUB;
+        if (aligned && s0 + SUB <= n) {
             mbar_arrive_expect_tx(&T.bars[s], SUBB);
-            bulk_g2s(stage + s * SUBB, a.one.sym + s0 * sizeof(Sym), SUBB, &T.bars[s]);
+            bulk_g2s(stage + s * SUBB, sym + s0 * sizeof(Sym), SUBB, &T.bars[s]);
         } else {
             mbar_arrive(&T.bars[s]);
         }
@@ -270,9 +314,12 @@ __device__ __forceinline__ void seg_produce(const EncArgs &a, SegProducer &p, ui
 // The 8 merge warps of the segment path.  TAB 0: codebook entries in shared
 // memory (tab[s & tmask]); TAB 2: the 32-bit entries in global memory.  MANY:
 // chunks shorter than a segment (several chunk boundaries per segment).
-template <typename Sym, int TAB, int R2, bool MANY>
+// BATCH: tiles of many fields (sfirst: their first tile ids; TAB 2 with each
+// field's own entries); the field's values are read per tile.  LONG: some
+// codeword has more than 23 bits (flag entries).
+template <typename Sym, int TAB, int R2, bool MANY, bool BATCH, bool LONG>
 __device__ __forceinline__ void seg_merge(const EncArgs &a, uint8_t *stage, uint32_t *ring, const uint32_t *tab,
-                                          uint32_t total, SegShared &T) {
+                                          uint32_t total, SegShared &T, const uint32_t *sfirst) {
     constexpr int V = VecOf<Sym>::N;
     constexpr int NV = SegGeom<Sym>::NV;
     constexpr int NST = SegGeom<Sym>::NST;
@@ -286,17 +333,20 @@ __device__ __forceinline__ void seg_merge(const EncArgs &a, uint8_t *stage, uint
     constexpr int NW = kEncThreads / 32;
     static_assert(RL <= V, "a run stays inside one vector");
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const EncField &F = a.one;
     const uint32_t tmask = a.tslots - 1;
-    const uint64_t n = F.n;
-    const uint32_t nbins = F.nbins;
-    const Sym *symp = reinterpret_cast<const Sym *>(F.sym);
-    uint32_t *status = F.status;
-    const int M = F.chunk_log2;
-    const uint32_t cmask = (1u << M) - 1;            // M <= 30
-    uint64_t *offs = F.offs;
+    // the field's values (per tile in a batched launch)
+    uint64_t n = a.one.n;
+    uint32_t nbins = a.one.nbins;
+    const Sym *symp = reinterpret_cast<const Sym *>(a.one.sym);
+    uint32_t *status = a.one.status;
+    int M = a.one.chunk_log2;
+    uint32_t cmask = (1u << M) - 1;                  // M <= 30
+    uint64_t *offs = a.one.offs;
+    bool faligned = a.one.aligned;
+    bool csm = seg_coff_smem<Sym>(M);
+    const uint8_t *bookp = a.one.book;
+    if constexpr (BATCH) status = a.fields[0].status;
     volatile uint32_t *stage_tile = T.stage_tile;
-    const bool csm = seg_coff_smem<Sym>(M);
     const uint32_t stage_s = smem_u32(stage), ring_s = smem_u32(ring);
     const uint32_t tab_s = TAB == 2 ? 0u : smem_u32(tab);
     const uint32_t rmask = sizeof(Sym) == 1 ? ~(tmask * 0x01010101u)
@@ -305,7 +355,7 @@ __device__ __forceinline__ void seg_merge(const EncArgs &a, uint8_t *stage, uint
     SegProducer prod{0u, 0u};
     if (tid == 0) {
         prod.next = take_tile(a);
-        for (int i = 0; i < NST; i++) seg_produce<Sym>(a, prod, total, stage, T);
+        for (int i = 0; i < NST; i++) seg_produce<Sym, BATCH>(a, prod, total, stage, T, sfirst);
     }
     merge_sync();
 
@@ -331,10 +381,28 @@ __device__ __forceinline__ void seg_merge(const EncArgs &a, uint8_t *stage, uint
             }
             break;
         }
+        uint32_t j = g;                                         // the tile within its field
+        uint32_t fld = 0;
+        if constexpr (BATCH) {
+            fld = reinterpret_cast<volatile uint32_t *>(T.stage_field)[s];
+            const EncField &Fb = a.fields[fld];
+            j = g - sfirst[fld];
+            n = Fb.n;
+            nbins = Fb.nbins;
+            symp = reinterpret_cast<const Sym *>(Fb.sym);
+            status = Fb.status;
+            M = Fb.chunk_log2;
+            cmask = (1u << M) - 1;
+            offs = Fb.offs;
+            faligned = Fb.aligned;
+            csm = seg_coff_smem<Sym>(M);
+            tab = Fb.etab;
+            bookp = Fb.book;
+        }
         if (!mbar_wait_bounded(&T.bars[s], sph)) set_error(status, HUFF_ERR_TIMEOUT);
         // symbol indices fit 32 bits (n < 2^32)
-        const uint32_t s0 = g * SUB;
-        const bool full = F.aligned && (uint64_t)s0 + SUB <= n;
+        const uint32_t s0 = j * SUB;
+        const bool full = faligned && (uint64_t)s0 + SUB <= n;
         const uint32_t q0 = s0 + tid * SEG;                     // first symbol of this segment
 
         // ---- reduce-merge of the segment into NR runs
@@ -380,6 +448,30 @@ __device__ __forceinline__ void seg_merge(const EncArgs &a, uint8_t *stage, uint
             }
             set_error(status, code);
         }
+        if (LONG && (bad & kLong32)) {
+            // a codeword over 23 bits: this segment's runs from the codebook's
+            // 64-bit codewords (the last 64 bits of each run, and its length)
+            const uint64_t *gcw = reinterpret_cast<const uint64_t *>(bookp + cb_cw_offset());
+#pragma unroll
+            for (int q = 0; q < NR; q++) {
+                uint64_t acc = 0;
+                uint32_t len = 0;
+#pragma unroll
+                for (int x = 0; x < RL; x++) {
+                    const uint64_t i = q0 + (uint64_t)(q * RL + x);
+                    if (i < n) {
+                        const uint32_t sy = (uint32_t)symp[i];
+                        const uint64_t cw = sy < nbins ? gcw[sy] : 0ull;
+                        const uint32_t l = (uint32_t)(cw >> HUFF_CW_LEN_SHIFT);
+                        acc = (acc << l) | (cw & ((1ull << l) - 1));
+                        len += l;
+                    }
+                }
+                hi[q] = (uint32_t)(acc >> 32);
+                lo[q] = (uint32_t)acc;
+                rb[q] = len;
+            }
+        }
 
         // ---- the segment's length and last 32 bits
         uint32_t L = 0, tail = 0;
@@ -413,7 +505,7 @@ __device__ __forceinline__ void seg_merge(const EncArgs &a, uint8_t *stage, uint
         if (lane == 0) ptail = 0;
         merge_sync();
         // every merge thread has read stage s: refill it
-        if (tid == 0) seg_produce<Sym>(a, prod, total, stage, T);
+        if (tid == 0) seg_produce<Sym, BATCH>(a, prod, total, stage, T, sfirst);
         const uint32_t wl = lane < (uint32_t)NW ? T.wlen[pb][lane] : 0u;
         const uint32_t wt = lane < (uint32_t)NW ? T.wtail[pb][lane] : 0u;
         uint32_t wi = wl;
@@ -455,10 +547,10 @@ __device__ __forceinline__ void seg_merge(const EncArgs &a, uint8_t *stage, uint
         if (tid == 0) {
             if (!room) set_error(status, HUFF_ERR_NOT_IN_CODEBOOK);
             st_relaxed_u64(&a.desc[2 * (uint64_t)g], kFlagAgg | ((uint64_t)last32 << 24) | Lt);
-            if (g == 0) st_relaxed_u64(&a.desc[1], kFlagPre | Lt);
+            if (j == 0) st_relaxed_u64(&a.desc[2 * (uint64_t)g + 1], kFlagPre | Lt);   // a field's first tile
             T.slot[sl].g = g;
-            T.slot[sl].f = 0;
-            T.slot[sl].j = g;
+            T.slot[sl].f = fld;
+            T.slot[sl].j = j;
             T.slot[sl].L = Lt;
             T.slot[sl].base = head;
             T.slot[sl].pad = Wa;
@@ -509,7 +601,9 @@ __device__ __forceinline__ void seg_merge(const EncArgs &a, uint8_t *stage, uint
                     seg_put(cur, e5, wa, hi[q], lo[q], rb[q]);
                 } else {
                     SegPut st{cur, e5, wa};
-                    st = seg_put_long<Sym, TAB>(st, symp, q0 + ((uint64_t)q << R2), RL, n, tab, tab_s, nbins, tmask);
+                    st = seg_put_long<Sym, TAB>(st, symp, q0 + ((uint64_t)q << R2), RL, n, tab, tab_s, nbins, tmask,
+                                                LONG ? reinterpret_cast<const uint64_t *>(bookp + cb_cw_offset())
+                                                     : nullptr);
                     cur = st.cur;
                     e5 = st.e5;
                     wa = st.wa;
@@ -534,9 +628,10 @@ __device__ __forceinline__ void seg_merge(const EncArgs &a, uint8_t *stage, uint
 // last, so one lane waits for it alone before the window is read.
 // A tile that has not published after
 // spin_limit polls records HUFF_ERR_TIMEOUT and the look-back goes on with
-// what it has (the stream is then invalid).
+// what it has (the stream is then invalid).  lo: the field's first tile (0
+// for a single field); tiles before it count as a prefix of 0.
 static __device__ uint64_t seg_lookback(uint64_t *desc, uint32_t *status, uint64_t j, uint64_t L, uint32_t *prev,
-                                        uint32_t spin_limit) {
+                                        uint32_t spin_limit, uint64_t lo) {
     const uint32_t lane = threadIdx.x & 31;
     uint64_t excl = 0;
     int64_t base = (int64_t)j;                 // look at tiles [base - 128, base)
@@ -560,8 +655,8 @@ static __device__ uint64_t seg_lookback(uint64_t *desc, uint32_t *status, uint64
         for (int q = kLbPer - 1; q >= 0; q--) {
             const uint32_t key = kLbPer * lane + q;
             const int64_t idx = base - 1 - (int64_t)key;
-            uint64_t agg = 0, pre = kFlagPre;  // before tile 0: prefix 0
-            if (idx >= 0) ld_desc(&desc[2 * idx], agg, pre);
+            uint64_t agg = 0, pre = kFlagPre;  // before the field's first tile: prefix 0
+            if (idx >= (int64_t)lo) ld_desc(&desc[2 * idx], agg, pre);
             if (idx == (int64_t)j - 1) a1 = agg;
             if (pre) {
                 pkey = key;
@@ -611,9 +706,9 @@ static __device__ uint64_t seg_lookback(uint64_t *desc, uint32_t *status, uint64
 // tile's words, they are copied from the ring into the dense stream and the
 // offset is added to the tile's chunk offsets; the tile's ring words and slot
 // are then freed in tile order (after the previous tile, another warp's).
-template <typename Sym>
-__device__ void seg_helper(const EncArgs &a, const EncField &F, uint32_t *ring, uint32_t total, SegShared &T,
-                           uint32_t k) {
+template <typename Sym, bool BATCH>
+__device__ void seg_helper(const EncArgs &a, const EncField &F0, uint32_t *ring, uint32_t total, SegShared &T,
+                           uint32_t k, const uint32_t *sfirst) {
     constexpr uint32_t RW = SegGeom<Sym>::RW;
     constexpr uint32_t SUB = seg_sub_syms<Sym>();
     const uint32_t lane = threadIdx.x & 31;
@@ -623,18 +718,21 @@ __device__ void seg_helper(const EncArgs &a, const EncField &F, uint32_t *ring, 
         const uint32_t sl = t % kSegSlots;
         const uint32_t ph = (t / kSegSlots) & 1;
         if (!mbar_wait_bounded(&T.full[sl], ph)) {
-            if (lane == 0) set_error(F.status, HUFF_ERR_TIMEOUT);
+            if (lane == 0) set_error(BATCH ? a.fields[0].status : F0.status, HUFF_ERR_TIMEOUT);
             return;
         }
         const uint32_t g = T.slot[sl].g;
         if (g >= total) return;
         const uint64_t j = T.slot[sl].j;
         const uint32_t L = T.slot[sl].L, base = T.slot[sl].base, Wa = T.slot[sl].pad;
+        const uint32_t fld = T.slot[sl].f;
+        const EncField &F = BATCH ? a.fields[fld] : F0;
+        const uint64_t ntiles = BATCH ? (uint64_t)(sfirst[fld + 1] - sfirst[fld]) : (uint64_t)F.ntiles;
         uint64_t G = 0;
         uint32_t prev = 0;
-        if (j > 0) G = seg_lookback(a.desc, F.status, j, L, &prev, spin);
+        if (j > 0) G = seg_lookback(a.desc, F.status, g, L, &prev, spin, (uint64_t)g - j);
         prev = __shfl_sync(0xFFFFFFFFu, prev, 0);
-        const bool last = (j == F.ntiles - 1);
+        const bool last = (j == ntiles - 1);
         if (last && lane == 0) {
             F.offs[F.nchunks] = G + L;
             *F.total_bits = G + L;
@@ -675,7 +773,9 @@ __device__ void seg_helper(const EncArgs &a, const EncField &F, uint32_t *ring, 
         const uint64_t tend = t0 + SUB < F.n ? t0 + SUB : F.n;
         const uint64_t c_end = (tend + chunk_mask) >> M;
         uint64_t *offs = F.offs;
-        if (seg_coff_smem<Sym>(M)) {
+        // (a batched launch with short chunks in some field writes every
+        // field's chunk offsets to global memory)
+        if (seg_coff_smem<Sym>(M) && !(BATCH && a.seg_many)) {
             if (c_first + lane < c_end) offs[c_first + lane] = T.coff[sl][lane] + G;
         } else {
             for (uint64_t c = c_first + lane; c < c_end; c += 32) offs[c] += G;
@@ -695,31 +795,54 @@ __device__ void seg_helper(const EncArgs &a, const EncField &F, uint32_t *ring, 
     }
 }
 
-template <typename Sym, int TAB, int R2>
-__device__ __forceinline__ void seg_merge_m(bool many, const EncArgs &a, uint8_t *stage, uint32_t *ring,
-                                            const uint32_t *tab, uint32_t total, SegShared &T) {
-    if (many) seg_merge<Sym, TAB, R2, true>(a, stage, ring, tab, total, T);
-    else seg_merge<Sym, TAB, R2, false>(a, stage, ring, tab, total, T);
+// The merge loop of a field with codewords over 23 bits, out of line: its
+// registers are allocated apart from the common loop's.  The launch's
+// arguments are passed by value, so that the kernel's own copy keeps no
+// address (which would move it to local memory for the common loop too).
+template <typename Sym, int TAB, int R2, bool MANY, bool BATCH>
+__device__ __noinline__ void seg_merge_long(const EncArgs a, uint8_t *stage, uint32_t *ring, const uint32_t *tab,
+                                            uint32_t total, SegShared &T, const uint32_t *sfirst) {
+    seg_merge<Sym, TAB, R2, MANY, BATCH, true>(a, stage, ring, tab, total, T, sfirst);
 }
 
-template <typename Sym, int TAB>
-__device__ __forceinline__ void seg_merge_r(int r, bool many, const EncArgs &a, uint8_t *stage, uint32_t *ring,
-                                            const uint32_t *tab, uint32_t total, SegShared &T) {
-    if constexpr (sizeof(Sym) == 1) {
-        if (r <= 2) seg_merge_m<Sym, TAB, 2>(many, a, stage, ring, tab, total, T);
-        else if (r == 3) seg_merge_m<Sym, TAB, 3>(many, a, stage, ring, tab, total, T);
-        else seg_merge_m<Sym, TAB, 4>(many, a, stage, ring, tab, total, T);
-    } else if constexpr (sizeof(Sym) == 2) {
-        if (r <= 2) seg_merge_m<Sym, TAB, 2>(many, a, stage, ring, tab, total, T);
-        else seg_merge_m<Sym, TAB, 3>(many, a, stage, ring, tab, total, T);
+// LONGI: the long instance inline (the kernel is then allocated for it) or
+// out of line.
+template <typename Sym, int TAB, int R2, bool BATCH, bool LONGI>
+__device__ __forceinline__ void seg_merge_m(bool many, bool lng, const EncArgs &a, uint8_t *stage, uint32_t *ring,
+                                            const uint32_t *tab, uint32_t total, SegShared &T,
+                                            const uint32_t *sfirst) {
+    if (LONGI && lng) {
+        if (many) seg_merge<Sym, TAB, R2, true, BATCH, true>(a, stage, ring, tab, total, T, sfirst);
+        else seg_merge<Sym, TAB, R2, false, BATCH, true>(a, stage, ring, tab, total, T, sfirst);
+    } else if (lng) {
+        if (many) seg_merge_long<Sym, TAB, R2, true, BATCH>(a, stage, ring, tab, total, T, sfirst);
+        else seg_merge_long<Sym, TAB, R2, false, BATCH>(a, stage, ring, tab, total, T, sfirst);
     } else {
-        if (r <= 1) seg_merge_m<Sym, TAB, 1>(many, a, stage, ring, tab, total, T);
-        else seg_merge_m<Sym, TAB, 2>(many, a, stage, ring, tab, total, T);
+        if (many) seg_merge<Sym, TAB, R2, true, BATCH, false>(a, stage, ring, tab, total, T, sfirst);
+        else seg_merge<Sym, TAB, R2, false, BATCH, false>(a, stage, ring, tab, total, T, sfirst);
+    }
+}
+
+template <typename Sym, int TAB, bool BATCH = false, bool LONGI = false>
+__device__ __forceinline__ void seg_merge_r(int r, bool many, bool lng, const EncArgs &a, uint8_t *stage,
+                                            uint32_t *ring, const uint32_t *tab, uint32_t total, SegShared &T,
+                                            const uint32_t *sfirst = nullptr) {
+    if constexpr (sizeof(Sym) == 1) {
+        if (r <= 2) seg_merge_m<Sym, TAB, 2, BATCH, LONGI>(many, lng, a, stage, ring, tab, total, T, sfirst);
+        else if (r == 3) seg_merge_m<Sym, TAB, 3, BATCH, LONGI>(many, lng, a, stage, ring, tab, total, T, sfirst);
+        else seg_merge_m<Sym, TAB, 4, BATCH, LONGI>(many, lng, a, stage, ring, tab, total, T, sfirst);
+    } else if constexpr (sizeof(Sym) == 2) {
+        if (r <= 2) seg_merge_m<Sym, TAB, 2, BATCH, LONGI>(many, lng, a, stage, ring, tab, total, T, sfirst);
+        else seg_merge_m<Sym, TAB, 3, BATCH, LONGI>(many, lng, a, stage, ring, tab, total, T, sfirst);
+    } else {
+        if (r <= 1) seg_merge_m<Sym, TAB, 1, BATCH, LONGI>(many, lng, a, stage, ring, tab, total, T, sfirst);
+        else seg_merge_m<Sym, TAB, 2, BATCH, LONGI>(many, lng, a, stage, ring, tab, total, T, sfirst);
     }
 }
 
 // The segment path of a single-field launch (the header already checked).
-template <typename Sym, bool GTAB>
+// LONGOK: codewords over 23 bits take the segment path too (inline).
+template <typename Sym, bool GTAB, bool LONGOK>
 __device__ __forceinline__ void seg_body(const EncArgs &a, uint8_t *smem, SegShared &T,
                                          const huff_codebook_header *hdr) {
     constexpr int NST = SegGeom<Sym>::NST;
@@ -748,11 +871,11 @@ __device__ __forceinline__ void seg_body(const EncArgs &a, uint8_t *smem, SegSha
         const uint64_t *gcw = reinterpret_cast<const uint64_t *>(a.one.book + cb_cw_offset());
         const uint32_t nb = a.one.nbins;
         for (uint32_t i = threadIdx.x; i < a.tslots; i += blockDim.x)
-            stab[i] = entry_from_cw<uint32_t>(i < nb ? gcw[i] : 0ull);
+            stab[i] = seg_entry_from_cw(i < nb ? gcw[i] : 0ull);
     }
     __syncthreads();
     if (threadIdx.x >= kEncThreads) {
-        seg_helper<Sym>(a, T.f0, ring, total, T, (threadIdx.x - kEncThreads) / 32);
+        seg_helper<Sym, false>(a, T.f0, ring, total, T, (threadIdx.x - kEncThreads) / 32, nullptr);
         return;
     }
     // the rule's word is the 32-bit ring word the runs are merged into, whatever
@@ -760,27 +883,73 @@ __device__ __forceinline__ void seg_body(const EncArgs &a, uint8_t *smem, SegSha
     int r = a.reduce_log2 >= 0 ? a.reduce_log2 : enc_rule_r(hdr->total_bits, hdr->nsymbols);
     r = r < seg_r_min<Sym>() ? seg_r_min<Sym>() : (r > seg_r_max<Sym>() ? seg_r_max<Sym>() : r);
     const bool many = (1ull << a.one.chunk_log2) < (uint64_t)seg_lane_syms<Sym>();
-    if (GTAB) seg_merge_r<Sym, 2>(r, many, a, stage, ring, a.etab, total, T);
-    else seg_merge_r<Sym, 0>(r, many, a, stage, ring, stab, total, T);
+    const bool lng = LONGOK && hdr->max_len > kSegEntryLen;
+    if (GTAB) seg_merge_r<Sym, 2, false, LONGOK>(r, many, lng, a, stage, ring, a.etab, total, T);
+    else seg_merge_r<Sym, 0, false, LONGOK>(r, many, lng, a, stage, ring, stab, total, T);
 }
 
 // Single-field encode: the segment path when the codebook allows it, else the
 // general encoder.  Dynamic shared memory: the larger of the two layouts.
-template <typename Sym, bool GTAB>
+// LONGOK: the segment path also takes codewords over 23 bits (the instance
+// batched plans launch per field); without it such fields run the general
+// encoder, and the common loop keeps registers the long one would take.
+template <typename Sym, bool GTAB, bool LONGOK>
 __global__ void __launch_bounds__(kSegThreads, 2) encode_one_kernel(EncArgs a) {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ EncShared S;
     __shared__ SegShared T;
     const huff_codebook_header *hdr = reinterpret_cast<const huff_codebook_header *>(a.one.book);
-    const bool seg = seg_fits<Sym>(hdr->max_len) && hdr->nbins == a.one.nbins && !fmt_chunk_aligned(a.one.format) &&
-                     (!GTAB || a.etab != nullptr);
-    if (seg) seg_body<Sym, GTAB>(a, smem, T, hdr);
+    const bool seg = seg_fits<Sym>(hdr->max_len) && (LONGOK || hdr->max_len <= kSegEntryLen) &&
+                     hdr->nbins == a.one.nbins && !fmt_chunk_aligned(a.one.format) && (!GTAB || a.etab != nullptr);
+    if (seg) seg_body<Sym, GTAB, LONGOK>(a, smem, T, hdr);
     else if (threadIdx.x < kEncCtaThreads) encode_body<Sym, GTAB, false, false>(a, smem, S);
+}
+
+// Batched segment form: one persistent launch over the segment tiles of
+// every field the planner gave them (first tile ids in a.seg_first, copied to
+// shared memory after the stages and the ring); each field's 32-bit entries
+// in global memory (EncField::etab); the reduction factor by rule over those
+// fields.  A launch with no such tiles returns at once.
+template <typename Sym>
+__host__ __device__ inline size_t seg_batch_smem_bytes(uint32_t nfields) {
+    return seg_smem_bytes<Sym>(1, true) + ((4ull * (nfields + 1) + 127) & ~127ull);
+}
+
+template <typename Sym>
+__global__ void __launch_bounds__(kSegThreads, 2) encode_seg_batch_kernel(EncArgs a) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    __shared__ SegShared T;
+    constexpr int NST = SegGeom<Sym>::NST;
+    uint8_t *stage = smem;
+    uint32_t *ring = reinterpret_cast<uint32_t *>(smem + NST * seg_sub_bytes<Sym>());
+    uint32_t *sfirst = ring + SegGeom<Sym>::RW + kSegRingPad;
+    for (uint32_t i = threadIdx.x; i <= a.nfields; i += blockDim.x) sfirst[i] = a.seg_first[i];
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NST; s++) mbar_init(&T.bars[s], 1);
+        for (int b = 0; b < kSegSlots; b++) {
+            mbar_init(&T.full[b], 1);
+            mbar_init(&T.done[b], kEncThreads);
+            mbar_init(&T.sfree[b], 1);
+        }
+        T.ring_tail = 0;
+        T.wdone = 0;
+        fence_barrier_init();
+    }
+    __syncthreads();
+    const uint32_t total = sfirst[a.nfields];
+    if (total == 0) return;
+    if (threadIdx.x >= kEncThreads) {
+        seg_helper<Sym, true>(a, T.f0, ring, total, T, (threadIdx.x - kEncThreads) / 32, sfirst);
+        return;
+    }
+    int r = a.conf->seg_r;
+    r = r < seg_r_min<Sym>() ? seg_r_min<Sym>() : (r > seg_r_max<Sym>() ? seg_r_max<Sym>() : r);
+    seg_merge_r<Sym, 2, true>(r, a.seg_many != 0, a.conf->seg_long != 0, a, stage, ring, nullptr, total, T, sfirst);
 }
 
 using EncOneFn = void (*)(EncArgs);
 // Instantiated per symbol width in encode_one_u{8,16,32}.cu.
 template <typename Sym>
-EncOneFn encode_one_kernel_get(bool gtab);
+EncOneFn encode_one_kernel_get(bool gtab, bool long_ok);
 
 }  // namespace huff

@@ -76,6 +76,7 @@ struct EncField {
     uint32_t ntiles;
     uint32_t tile_base;      // global id of the field's first tile
     uint32_t format;         // stream format (fmt_* below); 0 = dense 32-bit words
+    uint32_t *etab;          // batched segment form: room for the field's 32-bit codebook entries
 };
 
 // EncField::format: bits 0-1 code the unit width W (0: 32, 1: 16, 2: 8 bits),
@@ -88,7 +89,9 @@ struct EncBatchConf {
     uint32_t total_tiles;
     int32_t r;               // reduction factor for every field
     uint32_t entry32;        // every codeword fits the 32-bit table entry
-    uint32_t pad;
+    uint32_t seg_total;      // batched segment form: its tiles over all the fields it takes
+    int32_t seg_r;           // ... and its reduction factor (by rule over those fields)
+    uint32_t seg_long;       // ... some of those fields has codewords over 23 bits
 };
 
 // Checks the format fields of p (word_bits, layout, with chunk_log2 and merge)
@@ -105,16 +108,20 @@ huff_status encode_launch(const void *d_sym, uint64_t n, huff_dtype dtype, const
 // batched plan clears every field's with one memset).  min_tiles_per_cta: the
 // grid holds at most one CTA per that many tiles (concurrent launches of
 // many fields share the GPU; a CTA's start-up is paid once per CTA).
+// long_ok: the kernel instance whose segment path also takes codewords over
+// 23 bits (batched per-field launches; the plain instance keeps the common
+// loop's registers).
 huff_status encode_launch_ex(const void *d_sym, uint64_t n, huff_dtype dtype, const void *d_codebook, uint32_t nbins,
                              int chunk_log2, int reduce_log2, uint32_t format, uint32_t *d_out, uint64_t cap,
                              uint64_t *d_offs, uint64_t *d_total, uint8_t *scratch, uint32_t *status, cudaStream_t st,
                              uint32_t id_offset, uint32_t spin_limit, bool scratch_zeroed = false,
-                             uint32_t min_tiles_per_cta = 1);
+                             uint32_t min_tiles_per_cta = 1, bool long_ok = false);
 size_t encode_scratch_bytes(uint64_t n, uint32_t nbins);
 // Kernel launches of one encode_launch_ex call on a non-empty field.
 uint32_t encode_kernels_per_call(uint32_t nbins);
-// Sets the launch attributes encode_launch_ex needs for a dense field of this
-// dtype and alphabet size, so that later launches can be captured.
+// Sets the launch attributes encode_launch_ex (long_ok) needs for a dense
+// field of this dtype and alphabet size, so that later launches can be
+// captured.
 huff_status encode_prepare(huff_dtype dtype, uint32_t nbins);
 int encode_run_log2(huff_dtype dtype);
 // Symbols per sub-tile (the smallest tile) of a dtype.
@@ -122,8 +129,19 @@ uint32_t encode_sub_symbols(huff_dtype dtype);
 // Reduction factors the encoder supports for a dtype.
 void encode_r_range(huff_dtype dtype, int *r_min, int *r_max);
 huff_status encode_batch_prepare(huff_dtype dtype, uint32_t max_nbins, uint32_t nfields, int *ctas_per_sm);
+// Batched segment form (encode_seg.cuh): symbols per merge thread and per
+// tile; launch attributes; the entry tables and the persistent launch over
+// the segment tiles the planner laid out in seg_first.
+uint32_t encode_seg_lane_symbols(huff_dtype dtype);
+uint32_t encode_seg_tile_symbols(huff_dtype dtype);
+huff_status encode_seg_batch_prepare(huff_dtype dtype, uint32_t nfields);
+huff_status encode_seg_batch_launch(huff_dtype dtype, const EncField *d_fields, uint32_t nfields,
+                                    const EncBatchConf *d_conf, const uint32_t *seg_first, uint32_t max_nbins,
+                                    uint8_t *scratch, uint32_t grid, bool many, cudaStream_t st);
+// seg_first (nfields + 1 entries, or null): plan the batched segment form too.
 huff_status encode_batch_plan_launch(huff_dtype dtype, EncField *d_fields, uint32_t nfields, EncBatchConf *d_conf,
-                                     int r_override, uint32_t nsub_cap, cudaStream_t st);
+                                     int r_override, uint32_t nsub_cap, cudaStream_t st,
+                                     uint32_t *seg_first = nullptr);
 huff_status encode_batch_launch(huff_dtype dtype, const EncField *d_fields, uint32_t nfields,
                                 const EncBatchConf *d_conf, uint32_t max_nbins, uint8_t *scratch, uint32_t grid,
                                 cudaStream_t st);

@@ -92,7 +92,7 @@ def test_batch_plan_create_rejects_bad_fields_on_the_host(lib):
     out = ctypes.c_void_p()
     cfg = huff.huff_batch_cfg()
     L.huff_batch_default_cfg(ctypes.byref(cfg))
-    assert (cfg.autotune, cfg.reduce_log2, cfg.max_subtiles, cfg.ctas_per_sm, cfg.per_field) == (0, -1, 0, 0, 0)
+    assert (cfg.autotune, cfg.reduce_log2, cfg.max_subtiles, cfg.ctas_per_sm, cfg.encode_form) == (0, -1, 0, 0, 0)
     arr = (huff.huff_field * 1)()
     good = dict(d_sym=0x100000, n=1000, dtype=huff.HUFF_U16, nbins=1024, chunk_log2=10, d_out=0x200000,
                 out_capacity_words=1000, d_chunk_bit_offset=0x300000, d_total_bits=0x400000)
@@ -109,5 +109,5 @@ def test_batch_plan_create_rejects_bad_fields_on_the_host(lib):
     assert L.huff_batch_plan_create(arr, 0, ctypes.byref(cfg), None, ctypes.byref(out)) == 1
     for k, v in good.items():
         setattr(arr[0], k, v)
-    for bad_cfg in (huff.huff_batch_cfg(0, 7, 0, 0), huff.huff_batch_cfg(0, -1, 0, 0, 2)):
+    for bad_cfg in (huff.huff_batch_cfg(0, 7, 0, 0), huff.huff_batch_cfg(0, -1, 0, 0, 3)):
         assert L.huff_batch_plan_create(arr, 1, ctypes.byref(bad_cfg), None, ctypes.byref(out)) == 1

@@ -78,8 +78,8 @@ def _run_and_check(fields_np, nbins_list, **kw):
     return plan, fields
 
 
-@pytest.mark.parametrize("per_field", [False, True])
-def test_batch_u16_mixed_sizes_chunks_and_alignment(per_field):
+@pytest.mark.parametrize("form", [0, 1, 2])
+def test_batch_u16_mixed_sizes_chunks_and_alignment(form):
     """Fields of very different sizes (empty, one symbol, sub-tile and tile
     boundaries, up to 1.5 M symbols), mixed chunk sizes and two unaligned
     inputs, all in one batch; with one persistent encode launch and with one
@@ -92,12 +92,12 @@ def test_batch_u16_mixed_sizes_chunks_and_alignment(per_field):
     offs[3] = 1
     offs[11] = 3
     plan, _ = _run_and_check(fields_np, [1024] * len(sizes), chunk_list=chunks, offsets_elems=offs,
-                             per_field=per_field)
-    assert plan.info()["per_field"] == int(per_field)
+                             encode_form=form)
+    assert plan.info()["encode_form"] == form
 
 
-@pytest.mark.parametrize("per_field", [False, True])
-def test_batch_dtypes_and_alphabet_classes(per_field):
+@pytest.mark.parametrize("form", [0, 1, 2])
+def test_batch_dtypes_and_alphabet_classes(form):
     """u8, u16 and u32 fields over small, medium (table in global memory) and
     large (packed histogram counters) alphabets in one plan: one launch group
     per dtype and alphabet class."""
@@ -112,7 +112,7 @@ def test_batch_dtypes_and_alphabet_classes(per_field):
                                     mapping=synth.permutation(3, K))); nbs.append(K)
     for j in range(2):
         fields_np.append(_field_input(30 + j, 123_457, 16384, 4, b=300.0)); nbs.append(16384)
-    plan, _ = _run_and_check(fields_np, nbs, per_field=per_field)
+    plan, _ = _run_and_check(fields_np, nbs, encode_form=form)
     assert plan.info()["groups"] >= 4
 
 
@@ -137,8 +137,40 @@ def test_batch_settings_do_not_change_output(r, cap, ctas):
     _run_and_check(fields_np, [1024] * len(sizes), reduce_log2=r, max_subtiles=cap, ctas_per_sm=ctas)
 
 
-@pytest.mark.parametrize("per_field", [False, True])
-def test_batch_rerun_with_new_contents(per_field):
+@pytest.mark.parametrize("form", [0, 1, 2])
+def test_batch_long_codewords_next_to_short_ones(form):
+    """Fields whose longest codewords have 24 to 28 bits (Fibonacci counts)
+    among ordinary ones, and u8 / u32 fields with 28-bit codewords: the
+    segment forms take the long codewords from the 64-bit codebook entries
+    (up to the ring's worst-case tile: 27 bits for u16, 42 for u8, 48 for
+    u32); the others stay with the general encoder."""
+    fields_np, nbs = [], []
+    for j, (dt, nb) in enumerate([(np.uint8, 256), (np.uint32, 4096)]):
+        fib = [1, 1]
+        while len(fib) < 29:
+            fib.append(fib[-1] + fib[-2])
+        ids = (np.arange(29, dtype=np.int64) * 7 + 3) % nb
+        a = np.repeat(ids, fib).astype(dt)
+        np.random.default_rng(100 + j).shuffle(a)
+        fields_np.append(a)
+        nbs.append(nb)
+    for j, nsym in enumerate([25, 26, 28, 29]):
+        fib = [1, 1]
+        while len(fib) < nsym:
+            fib.append(fib[-1] + fib[-2])
+        ids = (np.arange(nsym, dtype=np.int64) * 37 + 5) % 1024
+        a = np.repeat(ids, fib).astype(np.uint16)
+        np.random.default_rng(j).shuffle(a)
+        fields_np.append(a)
+        nbs.append(1024)
+    for j in range(3):
+        fields_np.append(_field_input(40 + j, 200_000 + 7 * j, 1024, 2))
+        nbs.append(1024)
+    _run_and_check(fields_np, nbs, encode_form=form)
+
+
+@pytest.mark.parametrize("form", [0, 1, 2])
+def test_batch_rerun_with_new_contents(form):
     """The plan captures pointers: new data in the same buffers gives the new
     data's encoding on the next run."""
     import paper_2010_10039_gb300 as huff
@@ -147,7 +179,7 @@ def test_batch_rerun_with_new_contents(per_field):
     a1 = [_field_input(j, n, 1024, 2, seed=1) for j, n in enumerate(sizes)]
     a2 = [_field_input(j, n, 1024, 2, b=9.0, seed=2) for j, n in enumerate(sizes)]
     fields = _make(a1, [1024] * 3)
-    plan = huff.BatchPlan(fields, per_field=per_field)
+    plan = huff.BatchPlan(fields, encode_form=form)
     plan.encode()
     torch.cuda.synchronize()
     for i in range(3):
@@ -162,8 +194,8 @@ def test_batch_rerun_with_new_contents(per_field):
         _check_field(plan, i, fields[i], a2[i], 1024)
 
 
-@pytest.mark.parametrize("per_field", [False, True])
-def test_batch_errors_stay_in_their_field(per_field):
+@pytest.mark.parametrize("form", [0, 1, 2])
+def test_batch_errors_stay_in_their_field(form):
     """A symbol beyond its field's alphabet and an output buffer that is too
     small each mark only their own field; the other fields are exact."""
     import paper_2010_10039_gb300 as huff
@@ -176,7 +208,7 @@ def test_batch_errors_stay_in_their_field(per_field):
     nbs = [1024, 900, 1024, 1024]
     fields = _make(fields_np, nbs)
     fields[2]["out"] = fields[2]["out"][:100]     # far too small
-    plan = huff.BatchPlan(fields, per_field=per_field)
+    plan = huff.BatchPlan(fields, encode_form=form)
     plan.encode()
     torch.cuda.synchronize()
     st = plan.status()
@@ -196,16 +228,17 @@ def test_batch_more_than_one_group_of_fields():
     assert plan.info()["groups"] == 2
 
 
-@pytest.mark.parametrize("per_field", [False, True])
-def test_batch_launch_count_per_run(per_field):
+@pytest.mark.parametrize("form", [0, 1, 2])
+def test_batch_launch_count_per_run(form):
     import paper_2010_10039_gb300 as huff
     import torch
     fields_np = [_field_input(j, 10_000, 1024, 2) for j in range(3)] + [np.zeros(0, np.uint16)]
     fields = _make(fields_np, [1024] * 4)
-    plan = huff.BatchPlan(fields, per_field=per_field)
+    plan = huff.BatchPlan(fields, encode_form=form)
     k = plan.info()["kernels_per_run"]
-    # histogram and codebooks, then the tile planner and one encode, or one encode per non-empty field
-    assert k == (5 if per_field else 4)
+    # histogram and codebooks, then the tile planner and one encode; or one encode per non-empty field; or
+    # the planner, the entry tables, the segment encoder and the general encoder
+    assert k == {0: 4, 1: 5, 2: 6}[form]
     c0 = huff.huff_launch_count()
     plan.encode()
     torch.cuda.synchronize()

@@ -184,6 +184,32 @@ def test_long_codewords_fibonacci():
     assert np.array_equal(r.offs_np(), offs)
 
 
+def _fibonacci_field(nsym, nbins, dtype, seed):
+    """A field whose histogram is F1..F(nsym) on nsym ids spread over the
+    alphabet: its longest codeword has nsym - 1 bits."""
+    fib = [1, 1]
+    while len(fib) < nsym:
+        fib.append(fib[-1] + fib[-2])
+    ids = (np.arange(nsym, dtype=np.int64) * 37 + 5) % nbins
+    sym = np.repeat(ids, fib).astype(dtype)
+    np.random.default_rng(seed).shuffle(sym)
+    return sym
+
+
+@pytest.mark.parametrize("max_len", [23, 24, 25, 27, 28])
+@pytest.mark.parametrize("width", [1, 2])
+def test_codewords_just_over_the_table_entry(max_len, width):
+    """Longest codewords of 23 to 28 bits through the plain calls: up to 23
+    bits the segment path, above it the general encoder of the same launch
+    (the batched per-field form takes them on the segment path: see
+    test_gpu_batch)."""
+    nb = 256 if width == 1 else 1024
+    sym = _fibonacci_field(max_len + 1, nb, np.uint8 if width == 1 else np.uint16, max_len)
+    r, want, words, tb = _full_check(sym, nb)
+    assert want["max_len"] == max_len
+    assert np.array_equal(oracle.decode(words, tb, sym.size, want, width=width), sym)
+
+
 def test_error_symbol_out_of_range():
     import paper_2010_10039_gb300 as huff
     sym = synth.laplace_field(50_000, seed=4)
