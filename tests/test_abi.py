@@ -111,3 +111,36 @@ def test_batch_plan_create_rejects_bad_fields_on_the_host(lib):
         setattr(arr[0], k, v)
     for bad_cfg in (huff.huff_batch_cfg(0, 7, 0, 0), huff.huff_batch_cfg(0, -1, 0, 0, 3)):
         assert L.huff_batch_plan_create(arr, 1, ctypes.byref(bad_cfg), None, ctypes.byref(out)) == 1
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every struct the Python binding declares has the size and field
+    offsets the C header gives it (compiled here with gcc), so the binding
+    and libhuff.so agree on the records they exchange."""
+    import shutil
+    import subprocess
+    import paper_2010_10039_gb300 as huff
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [huff.huff_params, huff.huff_field, huff.huff_batch_cfg, huff.huff_batch_info,
+               huff.huff_serve_cfg, huff.huff_request, huff.huff_result, huff.huff_serve_stats]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "huff.h"', "int main(void) {"]
+    for st in structs:
+        name = st.__name__
+        lines.append(f'    printf("{name} %zu\\n", sizeof({name}));')
+        for field, _ in st._fields_:
+            lines.append(f'    printf("{name}.{field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    include = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run([cc, "-std=c11", "-I", include, str(src), "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                       text=True).stdout.splitlines())
+    for st in structs:
+        name = st.__name__
+        assert int(got[name]) == ctypes.sizeof(st), name
+        for field, _ in st._fields_:
+            assert int(got[f"{name}.{field}"]) == getattr(st, field).offset, f"{name}.{field}"
